@@ -1,0 +1,134 @@
+/*
+ * vfe.h -- C ABI of the GB300 voxel finite-element elastic wave solver.
+ *
+ * The library advances the explicit structured-mesh elastic wave equation of
+ * Ichimura et al., arXiv 2404.13683: the element-by-element internal force
+ * f = K u over a voxel mesh (Section 2, Eq. DGE:ORG) followed by the
+ * central-difference update with a diagonal mass matrix (Eq. eqtimehistory,
+ * and its rearranged update form in Section 3).
+ *
+ * Two element kinds are supported: the conventional lumped-mass trilinear
+ * voxel element VFEM and the orthogonal voxel element OVFEM (Eqs. OVFEMstiff,
+ * OVFEMmass, OVFEMbasis1, OVFEMbasis2).  Two arithmetic paths are supported:
+ *   VFE_PATH_FP64  plain FP64 on CUDA cores (both element kinds);
+ *   VFE_PATH_TC    OVFEM only: K u formed as exact integer-split tensor-core
+ *                  products in the spirit of Eq. GE:TC and Eqs.
+ *                  int8comp1-int8comp2 (see vfe_options.stages).
+ *
+ * Conventions shared by every call:
+ *   - grid: nx*ny*nz cubic elements of side h; nodes (i,j,k), 0<=i<=nx etc.;
+ *     node id = i + (nx+1)*(j + (ny+1)*k); element id = i + nx*(j + ny*k);
+ *     z is up and k = 0 is the bottom plane;
+ *   - nodal vectors are FP64 arrays [n_nodes][3] (component fastest);
+ *   - material_table rows are {Vp, Vs, rho} (m/s, m/s, kg/m^3); an element id
+ *     of -1 marks a void cell (no stiffness, no mass);
+ *   - every call returns VFE_OK (0) or a negative VFE_E* code; the message of
+ *     the last failure on the calling thread is vfe_last_error();
+ *   - the library copies every input array; the caller owns every output
+ *     buffer; pointers are host pointers unless stated otherwise;
+ *   - calls on one mesh must not run concurrently from several threads.
+ */
+#ifndef VFE_H
+#define VFE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VFE_OK 0
+#define VFE_EINVAL (-1)   /* bad argument (message says which) */
+#define VFE_ENOMEM (-2)   /* host or device allocation failed */
+#define VFE_ECUDA (-3)    /* a CUDA call failed (message has the CUDA error) */
+#define VFE_ETIMEOUT (-4) /* a device-side bounded wait gave up; results invalid */
+#define VFE_ESTATE (-5)   /* call not valid in the current state */
+
+enum vfe_element_kind { VFE_OVFEM = 0, VFE_VFEM = 1 };
+enum vfe_path { VFE_PATH_FP64 = 0, VFE_PATH_TC = 1 };
+
+typedef struct vfe_options {
+  int element_kind; /* VFE_OVFEM (default) or VFE_VFEM */
+  int path;         /* VFE_PATH_TC (default) or VFE_PATH_FP64 */
+  int stages;       /* TC path: number of 11-bit integer digit stages, 1..5
+                       (default 5 = 55-bit split, >= the FP64 mantissa) */
+  int fix_bottom;   /* 1 (default): every node of plane k = 0 is fixed */
+  double dt;        /* time step; <= 0 selects cfl_fraction * critical step */
+  double cfl_fraction; /* default 0.5 */
+  int device;       /* CUDA device ordinal (default 0) */
+  void *stream;     /* cudaStream_t to run on; NULL = a stream the mesh owns */
+} vfe_options;
+
+typedef struct vfe_mesh vfe_mesh;
+
+/* Fill *opt with the defaults listed above. */
+void vfe_default_options(vfe_options *opt);
+
+/* Create a mesh.  material_ids: nx*ny*nz int32 (element order above, -1 =
+ * void); material_table: n_materials rows of {Vp, Vs, rho} with rho > 0,
+ * Vs >= 0 and Vp^2 > 4/3 Vs^2.  opt may be NULL for defaults.  Moduli follow
+ * Section 2: G = rho Vs^2, kappa = rho (Vp^2 - 4/3 Vs^2).  The critical step
+ * is 2/sqrt(max eigenvalue of M_e^-1 K_e) over the materials present.
+ * On success *out owns device memory until vfe_destroy. */
+int vfe_create_mesh(int nx, int ny, int nz, double h,
+                    const int32_t *material_ids, const double *material_table,
+                    int n_materials, const vfe_options *opt, vfe_mesh **out);
+
+/* Release everything the mesh owns.  NULL is accepted. */
+int vfe_destroy(vfe_mesh *mesh);
+
+/* Point force at node (i,j,k): F(t) = amp * ricker(t; f0, t0) * dir with the
+ * Ricker wavelet (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), applied
+ * as F^n at t = n dt (Section 3 uses an impulse force in z).  t0 <= 0 selects
+ * t0 = 1/f0.  Forces at a fixed or massless node are ignored. */
+int vfe_set_source(vfe_mesh *mesh, int i, int j, int k, const double dir[3],
+                   double f0_hz, double t0_s, double amp);
+
+/* Receivers at nodes ijk[n][3].  Resets the trace buffer: later vfe_step
+ * calls append u^{n+1} at every receiver for every step. */
+int vfe_set_receivers(vfe_mesh *mesh, int n, const int32_t *ijk);
+
+/* f = K u for the whole mesh (fixed DOFs included), u and f FP64 [nodes][3]
+ * host arrays.  Uses the mesh's path; does not touch the time-stepping state.
+ * Synchronous. */
+int vfe_internal_force(vfe_mesh *mesh, const double *u, double *f);
+
+/* Advance n >= 0 central-difference steps (Eq. eqtimehistory):
+ * u^{n+1} = 2u^n - u^{n-1} + dt^2 M^-1 (F^n - K u^n) on free DOFs.
+ * Asynchronous on the mesh's stream (launched as a captured CUDA graph);
+ * device errors surface at the next synchronising call. */
+int vfe_step(vfe_mesh *mesh, int n);
+
+/* Block until queued work is done; reports device-side timeouts. */
+int vfe_synchronize(vfe_mesh *mesh);
+
+/* Copy the traces recorded since vfe_set_receivers: out[s][r][3] FP64 for
+ * s < *n_steps_out (out may be NULL to query the count only).  Synchronous. */
+int vfe_get_traces(vfe_mesh *mesh, double *out, int64_t *n_steps_out);
+
+/* Time step in use, number of nodes, and steps taken since creation. */
+int vfe_get_dt(vfe_mesh *mesh, double *dt);
+int vfe_get_sizes(vfe_mesh *mesh, int64_t *n_nodes, int64_t *n_elements);
+int vfe_get_step_count(vfe_mesh *mesh, int64_t *steps);
+
+/* Read / replace the state (u^n, u^{n-1}) as FP64 [nodes][3] host arrays.
+ * Values at fixed or massless nodes are forced to zero by vfe_set_state. */
+int vfe_get_state(vfe_mesh *mesh, double *u, double *u_prev);
+int vfe_set_state(vfe_mesh *mesh, const double *u, const double *u_prev);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *vfe_last_error(void);
+
+/* Exact integer partial products of the TC path for a list of elements:
+ * out[q][48] int64 = (K^kappa q_e, K^G' q_e) for element ids[q], where
+ * q_e are the 24 integer inputs the kernel digitised from u at the given
+ * shift (q = floor(U / 2^shift) of the fixed-point state); both halves are
+ * stored in local DOF order 3a+c.  Diagnostic: lets tests check the tensor
+ * core arithmetic bit for bit.  TC path only; synchronous. */
+int vfe_debug_tc_partials(vfe_mesh *mesh, const double *u, int n,
+                          const int64_t *ids, int64_t *out, int *shift_out,
+                          int *frac_bits_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1028 @@
+// vfe_api.cu -- C ABI and host logic of the GB300 voxel FE wave solver.
+//
+// Host responsibilities: argument validation, element matrices (closed form
+// of Section 2's element stiffness), node masses, the CFL step, the
+// fixed-point scales of the tensor-core path, TMA tensor maps, work
+// decomposition, receivers, the Ricker source series, and stepping through
+// captured CUDA graphs.  Every step of the hot path runs in the kernels of
+// vfe_tc.cu / vfe_fp64.cu; there is no CPU fallback.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vfe_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(VFE_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));              \
+  } while (0)
+
+// ---- element matrices -------------------------------------------------------
+// Both voxel elements have the closed form
+//   S_kl(a,b) = 1/16 s^a_k s^b_l prod_{m not in {k,l}} (1 + alpha s^a_m s^b_m)
+//   K_(a,i),(b,j) = ds [lambda S_ij + G S_ji + G delta_ij sum_k S_kk]
+// with alpha = 3/4 for OVFEM (Heaviside phi, the seven psi stress bases) and
+// alpha = 1/3 for VFEM (trilinear phi, exact 2x2x2 Gauss).
+int sgn(int a, int k) { return ((a >> k) & 1) ? 1 : -1; }
+
+void element_matrix(int kind, double ds, double lambda, double G, double *K) {
+  const double alpha = kind == VFE_OVFEM ? 0.75 : 1.0 / 3.0;
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b) {
+      double S[3][3];
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+          double v = sgn(a, k) * sgn(b, l) / 16.0;
+          for (int m = 0; m < 3; ++m)
+            if (m != k && m != l) v *= 1.0 + alpha * sgn(a, m) * sgn(b, m);
+          S[k][l] = v;
+        }
+      const double tr = S[0][0] + S[1][1] + S[2][2];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          K[(3 * a + i) * 24 + 3 * b + j] =
+              ds * (lambda * S[i][j] + G * S[j][i] + (i == j ? G * tr : 0.0));
+    }
+}
+
+// Largest eigenvalue of a symmetric PSD 24x24 matrix: power iteration with a
+// Rayleigh quotient (the element matrices are tiny, so 20000 sweeps are cheap).
+double max_eigenvalue(const double *K) {
+  double v[24], w[24];
+  for (int i = 0; i < 24; ++i) v[i] = 1.0 + 0.01 * i * ((i % 3) - 1);
+  double lam = 0.0;
+  for (int it = 0; it < 20000; ++it) {
+    double nrm = 0.0;
+    for (int i = 0; i < 24; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < 24; ++j) acc += K[i * 24 + j] * v[j];
+      w[i] = acc;
+      nrm += acc * acc;
+    }
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) return 0.0;
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < 24; ++i) {
+      num += v[i] * w[i];
+      den += v[i] * v[i];
+    }
+    lam = num / den;
+    for (int i = 0; i < 24; ++i) v[i] = w[i] / nrm;
+  }
+  return lam;
+}
+
+double ricker(double t, double f0, double t0) {
+  const double a = M_PI * M_PI * f0 * f0 * (t - t0) * (t - t0);
+  return (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+const int64_t kSeriesChunk = 8192;
+
+}  // namespace
+
+struct vfe_mesh {
+  int nx = 0, ny = 0, nz = 0;
+  double h = 0.0;
+  vfe_options opt;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sms = 1;
+  int64_t nn = 0, ne = 0;
+  int n_mat = 0;
+  std::vector<double> kappa, G, rho;
+  std::vector<int32_t> mat;
+  std::vector<double> mass;
+  std::vector<char> fixed;
+  double dt = 0.0;
+  int64_t steps = 0;  // host mirror of the device step counter
+
+  int32_t *d_mat = nullptr;
+  int *d_status = nullptr;
+  double *d_series = nullptr;
+  double *d_traces = nullptr;
+  int64_t trace_cap = 0, trace_rows = 0;
+  int n_rec = 0;
+  std::vector<int64_t> rec_nodes;
+  std::vector<int32_t> rec_ijk;
+
+  bool has_src = false;
+  int64_t src_node = -1;
+  double src_dir[3] = {0, 0, 0}, f0 = 0, t0 = 0, amp = 0;
+  int cur = 0;  // which state buffer holds u^n
+
+  // FP64 path
+  double *d_u[2] = {nullptr, nullptr};
+  double *d_dt2m = nullptr;
+  double *d_K = nullptr;
+  int64_t *d_recnodes = nullptr;
+  void *d_f64params = nullptr;
+  int64_t *d_f64persist = nullptr;
+
+  // TC path
+  int nxp = 0, nyp = 0;
+  int64_t plane = 0, comp = 0;
+  int64_t *d_U[2] = {nullptr, nullptr};
+  int64_t *d_C = nullptr;
+  uint16_t *d_Bop = nullptr;
+  TcMaterial *d_mats = nullptr;
+  TcRecv *d_recv = nullptr;
+  int32_t *d_recv_off = nullptr;
+  unsigned long long *d_or = nullptr;
+  TcStepParams *d_tcparams = nullptr;
+  int64_t *d_tcpersist = nullptr;
+  CUtensorMap tmap[2];
+  int tiles_x = 0, tiles_y = 0, tiles_z = 0, cz = 0;
+  int e_ref = 0, eC = 0;
+  double src_scale = 0.0;  // dt^2 / m at the source node
+
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_valid[2] = {false, false};
+};
+
+static void invalidate_graphs(vfe_mesh *m) {
+  for (int i = 0; i < 2; ++i) {
+    if (m->graph[i]) cudaGraphExecDestroy(m->graph[i]);
+    m->graph[i] = nullptr;
+    m->graph_valid[i] = false;
+  }
+}
+
+static int64_t node_id(const vfe_mesh *m, int i, int j, int k) {
+  return (int64_t)i + (int64_t)(m->nx + 1) * ((int64_t)j + (int64_t)(m->ny + 1) * k);
+}
+
+// padded SoA index of node (i,j,k) in the TC nodal arrays (component 0)
+static int64_t tc_index(const vfe_mesh *m, int64_t n) {
+  const int64_t i = n % (m->nx + 1), j = (n / (m->nx + 1)) % (m->ny + 1),
+                k = n / ((int64_t)(m->nx + 1) * (m->ny + 1));
+  return k * m->plane + j * m->nxp + i;
+}
+
+static TcDevice tc_device(const vfe_mesh *m, int cur) {
+  TcDevice d;
+  memset(&d, 0, sizeof(d));
+  d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.nxp = m->nxp;
+  d.tiles_x = m->tiles_x; d.tiles_y = m->tiles_y; d.tiles_z = m->tiles_z; d.cz = m->cz;
+  d.n_mat = m->n_mat; d.stages = m->opt.stages; d.n_rec = m->n_rec;
+  d.plane = m->plane; d.comp = m->comp;
+  d.mat = m->d_mat; d.C = m->d_C;
+  d.U_prev = m->d_U[1 - cur]; d.U_next = m->d_U[1 - cur];
+  d.Bop = m->d_Bop; d.mats = m->d_mats; d.recv = m->d_recv; d.recv_off = m->d_recv_off;
+  d.src_node = m->has_src ? tc_index(m, m->src_node) : -1;
+  d.traces = m->d_traces; d.or_slots = m->d_or; d.status = m->d_status;
+  d.params = m->d_tcparams;
+  return d;
+}
+
+static F64Device f64_device(const vfe_mesh *m, int cur) {
+  F64Device d;
+  memset(&d, 0, sizeof(d));
+  d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.n_mat = m->n_mat; d.n_rec = m->n_rec;
+  d.nn = m->nn; d.mat = m->d_mat; d.K = m->d_K;
+  d.u = m->d_u[cur]; d.u_prev = m->d_u[1 - cur]; d.u_next = m->d_u[1 - cur];
+  d.dt2_m = m->d_dt2m; d.recv_nodes = m->d_recnodes; d.traces = m->d_traces;
+  d.src_node = m->has_src ? m->src_node : -1;
+  return d;
+}
+
+// one time step on the stream (prologue + kernel) starting from state cur
+static int enqueue_step(vfe_mesh *m, int cur) {
+  const int trace_on = m->n_rec > 0 ? 1 : 0;
+  if (m->opt.path == VFE_PATH_TC) {
+    CUDA_TRY(tc_launch_prologue_ex(m->stream, m->d_tcparams, m->d_tcpersist, m->d_series, m->d_or,
+                                   m->src_scale, m->src_dir, m->has_src ? 1 : 0, trace_on,
+                                   m->d_status));
+    TcDevice d = tc_device(m, cur);
+    CUDA_TRY(tc_launch_step(m->stream, d, &m->tmap[cur], TC_MODE_STEP));
+  } else {
+    double amp_dir[3] = {m->amp * m->src_dir[0], m->amp * m->src_dir[1], m->amp * m->src_dir[2]};
+    CUDA_TRY(f64_launch_prologue(m->stream, m->d_f64params, m->d_f64persist, m->d_series, amp_dir,
+                                 m->has_src ? 1 : 0, trace_on));
+    F64Device d = f64_device(m, cur);
+    CUDA_TRY(f64_launch_step(m->stream, d, m->d_f64params, 0));
+  }
+  return VFE_OK;
+}
+
+static int ensure_graph(vfe_mesh *m, int cur) {
+  if (m->graph_valid[cur]) return VFE_OK;
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_step(m, cur);
+  if (rc == VFE_OK) rc = enqueue_step(m, 1 - cur);
+  cudaError_t e = cudaStreamEndCapture(m->stream, &g);
+  if (rc != VFE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(VFE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&m->graph[cur], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess)
+    return fail(VFE_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  m->graph_valid[cur] = true;
+  return VFE_OK;
+}
+
+static int check_status(vfe_mesh *m) {
+  int st = 0;
+  CUDA_TRY(cudaMemcpy(&st, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & 1) return fail(VFE_ETIMEOUT, "a device-side wait timed out (status %d)", st);
+  if (st & 2) return fail(VFE_ETIMEOUT, "fixed-point shift out of range (status %d)", st);
+  return VFE_OK;
+}
+
+// ---- C ABI ------------------------------------------------------------------
+
+extern "C" {
+
+const char *vfe_last_error(void) { return g_last_error.c_str(); }
+
+void vfe_default_options(vfe_options *o) {
+  if (!o) return;
+  o->element_kind = VFE_OVFEM;
+  o->path = VFE_PATH_TC;
+  o->stages = TC_MAX_STAGES;
+  o->fix_bottom = 1;
+  o->dt = 0.0;
+  o->cfl_fraction = 0.5;
+  o->device = 0;
+  o->stream = nullptr;
+}
+
+int vfe_destroy(vfe_mesh *m) {
+  if (!m) return VFE_OK;
+  cudaSetDevice(m->device);
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  invalidate_graphs(m);
+  void *ptrs[] = {m->d_mat, m->d_status, m->d_series, m->d_traces, m->d_u[0], m->d_u[1],
+                  m->d_dt2m, m->d_K, m->d_recnodes, m->d_f64params, m->d_f64persist,
+                  m->d_U[0], m->d_U[1], m->d_C, m->d_Bop, m->d_mats, m->d_recv,
+                  m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+  delete m;
+  return VFE_OK;
+}
+
+static int build_tc(vfe_mesh *m);
+static int build_f64(vfe_mesh *m);
+static int rebuild_receivers(vfe_mesh *m);
+
+int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_ids,
+                    const double *material_table, int n_materials, const vfe_options *opt_in,
+                    vfe_mesh **out) {
+  if (!out) return fail(VFE_EINVAL, "out is NULL");
+  *out = nullptr;
+  vfe_options opt;
+  vfe_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(VFE_EINVAL, "grid must be at least 1x1x1");
+  if ((int64_t)nx * ny * nz > ((int64_t)1 << 31))
+    return fail(VFE_EINVAL, "grid too large (more than 2^31 elements)");
+  if (!(h > 0.0) || !std::isfinite(h)) return fail(VFE_EINVAL, "h must be positive");
+  if (!material_ids || !material_table) return fail(VFE_EINVAL, "NULL material array");
+  if (n_materials < 1) return fail(VFE_EINVAL, "n_materials must be >= 1");
+  if (opt.element_kind != VFE_OVFEM && opt.element_kind != VFE_VFEM)
+    return fail(VFE_EINVAL, "unknown element kind %d", opt.element_kind);
+  if (opt.path != VFE_PATH_FP64 && opt.path != VFE_PATH_TC)
+    return fail(VFE_EINVAL, "unknown path %d", opt.path);
+  if (opt.path == VFE_PATH_TC && opt.element_kind != VFE_OVFEM)
+    return fail(VFE_EINVAL, "the tensor-core path implements the orthogonal element only");
+  if (opt.path == VFE_PATH_TC && (opt.stages < 1 || opt.stages > TC_MAX_STAGES))
+    return fail(VFE_EINVAL, "stages must be in [1, %d]", TC_MAX_STAGES);
+  if (opt.path == VFE_PATH_TC && n_materials > TC_MAX_MAT)
+    return fail(VFE_EINVAL, "at most %d materials on the tensor-core path", TC_MAX_MAT);
+  if (opt.path == VFE_PATH_FP64 && n_materials > F64_MAX_MAT)
+    return fail(VFE_EINVAL, "at most %d materials on the FP64 path", F64_MAX_MAT);
+  if (!(opt.cfl_fraction > 0.0) || opt.cfl_fraction > 1.0)
+    return fail(VFE_EINVAL, "cfl_fraction must be in (0, 1]");
+
+  vfe_mesh *m = new vfe_mesh();
+  m->nx = nx; m->ny = ny; m->nz = nz; m->h = h; m->opt = opt; m->device = opt.device;
+  m->nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  m->ne = (int64_t)nx * ny * nz;
+  m->n_mat = n_materials;
+  m->kappa.resize(n_materials); m->G.resize(n_materials); m->rho.resize(n_materials);
+  for (int i = 0; i < n_materials; ++i) {
+    const double vp = material_table[3 * i], vs = material_table[3 * i + 1],
+                 rho = material_table[3 * i + 2];
+    if (!(rho > 0.0) || !(vs >= 0.0) || !(vp * vp > 4.0 / 3.0 * vs * vs) || !std::isfinite(vp) ||
+        !std::isfinite(rho)) {
+      delete m;
+      return fail(VFE_EINVAL, "material %d: need rho > 0, Vs >= 0, Vp^2 > 4/3 Vs^2", i);
+    }
+    m->G[i] = rho * vs * vs;
+    m->kappa[i] = rho * (vp * vp - 4.0 / 3.0 * vs * vs);
+    m->rho[i] = rho;
+  }
+  m->mat.assign(material_ids, material_ids + m->ne);
+  std::vector<char> used(n_materials, 0);
+  for (int64_t e = 0; e < m->ne; ++e) {
+    const int32_t v = m->mat[e];
+    if (v < -1 || v >= n_materials) {
+      delete m;
+      return fail(VFE_EINVAL, "material id %d at element %lld out of range", v, (long long)e);
+    }
+    if (v >= 0) used[v] = 1;
+  }
+  // node masses rho ds^3 / 8 per element corner (exact for OVFEM, lumped VFEM)
+  m->mass.assign(m->nn, 0.0);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const int32_t v = m->mat[i + (int64_t)nx * (j + (int64_t)ny * k)];
+        if (v < 0) continue;
+        const double me = m->rho[v] * h * h * h / 8.0;
+        for (int a = 0; a < 8; ++a)
+          m->mass[node_id(m, i + (a & 1), j + ((a >> 1) & 1), k + (a >> 2))] += me;
+      }
+  m->fixed.assign(m->nn, 0);
+  for (int64_t n = 0; n < m->nn; ++n) {
+    const int64_t k = n / ((int64_t)(nx + 1) * (ny + 1));
+    m->fixed[n] = (char)((opt.fix_bottom && k == 0) || m->mass[n] == 0.0);
+  }
+  // critical step over the materials present
+  double dtc = -1.0;
+  for (int i = 0; i < n_materials; ++i) {
+    if (!used[i]) continue;
+    double K[576];
+    element_matrix(opt.element_kind, h, m->kappa[i] - 2.0 * m->G[i] / 3.0, m->G[i], K);
+    const double lmax = max_eigenvalue(K) / (m->rho[i] * h * h * h / 8.0);
+    const double c = 2.0 / std::sqrt(lmax);
+    if (dtc < 0.0 || c < dtc) dtc = c;
+  }
+  if (dtc <= 0.0) {
+    delete m;
+    return fail(VFE_EINVAL, "the mesh has no solid element");
+  }
+  m->dt = opt.dt > 0.0 ? opt.dt : opt.cfl_fraction * dtc;
+
+  cudaError_t e = cudaSetDevice(m->device);
+  if (e != cudaSuccess) {
+    delete m;
+    return fail(VFE_ECUDA, "cudaSetDevice(%d): %s", opt.device, cudaGetErrorString(e));
+  }
+  int rc = VFE_OK;
+  do {
+    if (opt.stream) {
+      m->stream = reinterpret_cast<cudaStream_t>(opt.stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) { rc = fail(VFE_ECUDA, "stream: %s", cudaGetErrorString(e)); break; }
+      m->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
+    if ((e = cudaMalloc(&m->d_mat, sizeof(int32_t) * m->ne)) != cudaSuccess ||
+        (e = cudaMalloc(&m->d_status, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&m->d_series, sizeof(double) * kSeriesChunk)) != cudaSuccess) {
+      rc = fail(VFE_ENOMEM, "device allocation: %s", cudaGetErrorString(e));
+      break;
+    }
+    if ((e = cudaMemcpy(m->d_mat, m->mat.data(), sizeof(int32_t) * m->ne,
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(m->d_status, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(m->d_series, 0, sizeof(double) * kSeriesChunk)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "device upload: %s", cudaGetErrorString(e));
+      break;
+    }
+    rc = opt.path == VFE_PATH_TC ? build_tc(m) : build_f64(m);
+    if (rc == VFE_OK) rc = rebuild_receivers(m);
+  } while (0);
+  if (rc != VFE_OK) {
+    std::string msg = g_last_error;
+    vfe_destroy(m);
+    g_last_error = msg;
+    return rc;
+  }
+  *out = m;
+  return VFE_OK;
+}
+
+}  // extern "C"
+
+// ---- path-specific construction ---------------------------------------------
+
+static int build_f64(vfe_mesh *m) {
+  CUDA_TRY(f64_prepare());
+  std::vector<double> K((size_t)m->n_mat * 576);
+  for (int i = 0; i < m->n_mat; ++i)
+    element_matrix(m->opt.element_kind, m->h, m->kappa[i] - 2.0 * m->G[i] / 3.0, m->G[i],
+                   &K[(size_t)i * 576]);
+  std::vector<double> dt2m(m->nn, 0.0);
+  for (int64_t n = 0; n < m->nn; ++n)
+    if (!m->fixed[n]) dt2m[n] = m->dt * m->dt / m->mass[n];
+  CUDA_TRY(cudaMalloc(&m->d_K, sizeof(double) * K.size()));
+  CUDA_TRY(cudaMalloc(&m->d_dt2m, sizeof(double) * m->nn));
+  CUDA_TRY(cudaMalloc(&m->d_u[0], sizeof(double) * 3 * m->nn));
+  CUDA_TRY(cudaMalloc(&m->d_u[1], sizeof(double) * 3 * m->nn));
+  CUDA_TRY(cudaMalloc(&m->d_f64params, f64_params_bytes()));
+  CUDA_TRY(cudaMalloc(&m->d_f64persist, sizeof(int64_t) * 4));
+  CUDA_TRY(cudaMemcpy(m->d_K, K.data(), sizeof(double) * K.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->d_dt2m, dt2m.data(), sizeof(double) * m->nn, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(m->d_u[0], 0, sizeof(double) * 3 * m->nn));
+  CUDA_TRY(cudaMemset(m->d_u[1], 0, sizeof(double) * 3 * m->nn));
+  CUDA_TRY(cudaMemset(m->d_f64persist, 0, sizeof(int64_t) * 4));
+  return VFE_OK;
+}
+
+static int build_tc(vfe_mesh *m) {
+  const int nx = m->nx, ny = m->ny, nz = m->nz;
+  CUDA_TRY(tc_prepare());
+  // integer matrices K^kappa = 256/ds K_e(kappa=1,G=0), K^G' = 384/ds K_e(kappa=0,G=1)
+  double Kk[576], Kg[576];
+  element_matrix(VFE_OVFEM, 1.0, 1.0, 0.0, Kk);
+  element_matrix(VFE_OVFEM, 1.0, -2.0 / 3.0, 1.0, Kg);
+  int64_t Ik[576], Ig[576];
+  int64_t l1max = 0;
+  for (int r = 0; r < 24; ++r) {
+    int64_t l1 = 0;
+    for (int c = 0; c < 24; ++c) {
+      Ik[r * 24 + c] = llround(256.0 * Kk[r * 24 + c]);
+      Ig[r * 24 + c] = llround(384.0 * Kg[r * 24 + c]);
+      if (std::fabs(256.0 * Kk[r * 24 + c] - Ik[r * 24 + c]) > 1e-9 ||
+          std::fabs(384.0 * Kg[r * 24 + c] - Ig[r * 24 + c]) > 1e-9)
+        return fail(VFE_EINVAL, "internal: integer element matrix is not integral");
+      l1 += std::llabs(Ik[r * 24 + c]) + std::llabs(Ig[r * 24 + c]);
+    }
+    l1max = std::max(l1max, l1);
+  }
+  // node sums of up to 8 elements of (|P| A + |Q| B)/2^64 < 8 * l1 * 2^52 * 2^60 / 2^64
+  if (l1max >= 2048) return fail(VFE_EINVAL, "internal: element row norm too large");
+  // B operand image: core matrices (kg, ng) of 8 N-rows x 8 K-values (fp16)
+  std::vector<uint16_t> bop(TC_N * 32);
+  for (int kg = 0; kg < 4; ++kg)
+    for (int ng = 0; ng < 6; ++ng)
+      for (int r = 0; r < 8; ++r)
+        for (int l = 0; l < 8; ++l) {
+          const int n = 8 * ng + r;
+          const int go = n / 12, rem = n % 12, dxo = rem / 6, part = (rem % 6) / 3, co = rem % 3;
+          const int ao = dxo + 2 * (go & 1) + 4 * (go >> 1);
+          float v;
+          if (l >= 6) {
+            v = TC_MAGIC_B;
+          } else {
+            const int dx = l / 3, c = l % 3, dy = kg & 1, dz = kg >> 1;
+            const int col = 3 * (dx + 2 * dy + 4 * dz) + c, row = 3 * ao + co;
+            v = (float)(part == 0 ? Ik[row * 24 + col] : Ig[row * 24 + col]);
+          }
+          bop[((kg * 6 + ng) * 8 + r) * 8 + l] = __half_as_ushort(__float2half(v));
+        }
+  // per-material multipliers with a common unit 2^(64 - e_ref)
+  std::vector<TcMaterial> mats(m->n_mat);
+  std::vector<int> em(m->n_mat);
+  int e_ref = 1 << 30;
+  for (int i = 0; i < m->n_mat; ++i) {
+    const double kd = m->kappa[i] * m->h / 256.0, gd = m->G[i] * m->h / 384.0;
+    const double mx = std::max(kd, gd);
+    em[i] = 59 - std::ilogb(mx);
+    e_ref = std::min(e_ref, em[i]);
+  }
+  for (int i = 0; i < m->n_mat; ++i) {
+    mats[i].A = llrint(std::ldexp(m->kappa[i] * m->h / 256.0, em[i]));
+    mats[i].B = llrint(std::ldexp(m->G[i] * m->h / 384.0, em[i]));
+    mats[i].shift = std::min(em[i] - e_ref, 63);
+    mats[i].pad = 0;
+  }
+  m->e_ref = e_ref;
+  // per-node multiplier C = round(dt^2/m 2^eC), max in [2^61, 2^62)
+  double cmax = 0.0;
+  for (int64_t n = 0; n < m->nn; ++n)
+    if (!m->fixed[n]) cmax = std::max(cmax, m->dt * m->dt / m->mass[n]);
+  m->eC = 61 - std::ilogb(cmax);
+  // padded nodal layout (x pitch >= TMA box, y rows >= box)
+  m->nxp = ((std::max(nx + 1, TC_BOXX) + 3) / 4) * 4;
+  m->nyp = std::max(ny + 1, TC_NODES);
+  m->plane = (int64_t)m->nxp * m->nyp;
+  m->comp = m->plane * (nz + 1);
+  std::vector<int64_t> C(m->plane * (nz + 1), 0);
+  for (int64_t n = 0; n < m->nn; ++n)
+    if (!m->fixed[n]) C[tc_index(m, n)] = llrint(std::ldexp(m->dt * m->dt / m->mass[n], m->eC));
+  // work decomposition: choose the z chunk that minimises waves x layers
+  m->tiles_x = (nx + 1 + TC_OWN - 1) / TC_OWN;
+  m->tiles_y = (ny + 1 + TC_OWN - 1) / TC_OWN;
+  const int planes = nz + 1;
+  double best = 1e300;
+  for (int cz = 1; cz <= planes; ++cz) {
+    const int64_t items = (int64_t)m->tiles_x * m->tiles_y * ((planes + cz - 1) / cz);
+    const double waves = std::ceil((double)items / m->sms);
+    const double cost = waves * (cz + 1) + 0.02 * cz;
+    if (cost < best) { best = cost; m->cz = cz; }
+  }
+  m->tiles_z = (planes + m->cz - 1) / m->cz;
+
+  const size_t ubytes = sizeof(int64_t) * 3 * m->comp;
+  CUDA_TRY(cudaMalloc(&m->d_U[0], ubytes));
+  CUDA_TRY(cudaMalloc(&m->d_U[1], ubytes));
+  CUDA_TRY(cudaMalloc(&m->d_C, sizeof(int64_t) * C.size()));
+  CUDA_TRY(cudaMalloc(&m->d_Bop, sizeof(uint16_t) * bop.size()));
+  CUDA_TRY(cudaMalloc(&m->d_mats, sizeof(TcMaterial) * mats.size()));
+  CUDA_TRY(cudaMalloc(&m->d_or, sizeof(unsigned long long) * 3));
+  CUDA_TRY(cudaMalloc(&m->d_tcparams, sizeof(TcStepParams)));
+  CUDA_TRY(cudaMalloc(&m->d_tcpersist, sizeof(int64_t) * 8));
+  CUDA_TRY(cudaMemset(m->d_U[0], 0, ubytes));
+  CUDA_TRY(cudaMemset(m->d_U[1], 0, ubytes));
+  CUDA_TRY(cudaMemcpy(m->d_C, C.data(), sizeof(int64_t) * C.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->d_Bop, bop.data(), sizeof(uint16_t) * bop.size(),
+                      cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->d_mats, mats.data(), sizeof(TcMaterial) * mats.size(),
+                      cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(m->d_or, 0, sizeof(unsigned long long) * 3));
+  int64_t persist[8] = {0, 0, 0, 0, (int64_t)(m->eC + m->e_ref), 0, 0, 0};
+  CUDA_TRY(cudaMemcpy(m->d_tcpersist, persist, sizeof(persist), cudaMemcpyHostToDevice));
+  // TMA maps over the two state buffers: (x, y, z, component), int64, box 18x17x1x3
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled is not available");
+  for (int b = 0; b < 2; ++b) {
+    cuuint64_t dims[4] = {(cuuint64_t)m->nxp, (cuuint64_t)m->nyp, (cuuint64_t)(nz + 1), 3};
+    cuuint64_t strides[3] = {(cuuint64_t)m->nxp * 8, (cuuint64_t)m->plane * 8,
+                             (cuuint64_t)m->comp * 8};
+    cuuint32_t box[4] = {TC_BOXX, TC_NODES, 1, 3};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = enc(&m->tmap[b], CU_TENSOR_MAP_DATA_TYPE_INT64, 4, m->d_U[b], dims, strides, box,
+                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  }
+  return VFE_OK;
+}
+
+static int rebuild_receivers(vfe_mesh *m) {
+  // trace rows restart
+  m->trace_rows = 0;
+  if (m->opt.path == VFE_PATH_TC) {
+    int64_t persist2 = 0;
+    CUDA_TRY(cudaMemcpy(m->d_tcpersist + 2, &persist2, sizeof(int64_t), cudaMemcpyHostToDevice));
+    const int items = m->tiles_x * m->tiles_y * m->tiles_z;
+    std::vector<std::vector<TcRecv>> per(items);
+    for (int r = 0; r < m->n_rec; ++r) {
+      const int i = m->rec_ijk[3 * r], j = m->rec_ijk[3 * r + 1], k = m->rec_ijk[3 * r + 2];
+      const int tx = i / TC_OWN, ty = j / TC_OWN, tz = k / m->cz;
+      TcRecv v;
+      v.ei = (int16_t)(i - TC_OWN * tx);
+      v.ej = (int16_t)(j - TC_OWN * ty);
+      v.k = k;
+      v.r = r;
+      v.pad = 0;
+      per[tx + m->tiles_x * (ty + m->tiles_y * tz)].push_back(v);
+    }
+    std::vector<TcRecv> flat;
+    std::vector<int32_t> off(items + 1, 0);
+    for (int it = 0; it < items; ++it) {
+      if ((int)per[it].size() > TC_MAX_REC_CTA)
+        return fail(VFE_EINVAL, "more than %d receivers in one %dx%d node column chunk",
+                    TC_MAX_REC_CTA, TC_OWN, TC_OWN);
+      off[it] = (int32_t)flat.size();
+      flat.insert(flat.end(), per[it].begin(), per[it].end());
+    }
+    off[items] = (int32_t)flat.size();
+    if (m->d_recv) cudaFree(m->d_recv);
+    if (m->d_recv_off) cudaFree(m->d_recv_off);
+    m->d_recv = nullptr;
+    m->d_recv_off = nullptr;
+    CUDA_TRY(cudaMalloc(&m->d_recv, sizeof(TcRecv) * std::max<size_t>(flat.size(), 1)));
+    CUDA_TRY(cudaMalloc(&m->d_recv_off, sizeof(int32_t) * off.size()));
+    if (!flat.empty())
+      CUDA_TRY(cudaMemcpy(m->d_recv, flat.data(), sizeof(TcRecv) * flat.size(),
+                          cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->d_recv_off, off.data(), sizeof(int32_t) * off.size(),
+                        cudaMemcpyHostToDevice));
+  } else {
+    int64_t z = 0;
+    CUDA_TRY(cudaMemcpy(m->d_f64persist + 1, &z, sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (m->d_recnodes) cudaFree(m->d_recnodes);
+    m->d_recnodes = nullptr;
+    CUDA_TRY(cudaMalloc(&m->d_recnodes, sizeof(int64_t) * std::max(m->n_rec, 1)));
+    if (m->n_rec)
+      CUDA_TRY(cudaMemcpy(m->d_recnodes, m->rec_nodes.data(), sizeof(int64_t) * m->n_rec,
+                          cudaMemcpyHostToDevice));
+  }
+  invalidate_graphs(m);
+  return VFE_OK;
+}
+
+extern "C" {
+
+int vfe_set_source(vfe_mesh *m, int i, int j, int k, const double dir[3], double f0_hz,
+                   double t0_s, double amp) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  if (!dir) return fail(VFE_EINVAL, "dir is NULL");
+  if (i < 0 || j < 0 || k < 0 || i > m->nx || j > m->ny || k > m->nz)
+    return fail(VFE_EINVAL, "source node (%d,%d,%d) outside the grid", i, j, k);
+  if (!(f0_hz > 0.0) || !std::isfinite(amp) || !std::isfinite(t0_s))
+    return fail(VFE_EINVAL, "need f0 > 0 and finite t0, amp");
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  const int64_t n = node_id(m, i, j, k);
+  m->has_src = !m->fixed[n];
+  m->src_node = n;
+  for (int c = 0; c < 3; ++c) m->src_dir[c] = dir[c];
+  m->f0 = f0_hz;
+  m->t0 = t0_s > 0.0 ? t0_s : 1.0 / f0_hz;
+  m->amp = amp;
+  m->src_scale = m->has_src ? m->dt * m->dt / m->mass[n] : 0.0;
+  invalidate_graphs(m);
+  return VFE_OK;
+}
+
+int vfe_set_receivers(vfe_mesh *m, int n, const int32_t *ijk) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  if (n < 0 || (n > 0 && !ijk)) return fail(VFE_EINVAL, "bad receiver list");
+  for (int r = 0; r < n; ++r) {
+    const int i = ijk[3 * r], j = ijk[3 * r + 1], k = ijk[3 * r + 2];
+    if (i < 0 || j < 0 || k < 0 || i > m->nx || j > m->ny || k > m->nz)
+      return fail(VFE_EINVAL, "receiver %d at (%d,%d,%d) outside the grid", r, i, j, k);
+  }
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->n_rec = n;
+  m->rec_ijk.assign(ijk, ijk + 3 * (size_t)n);
+  m->rec_nodes.resize(n);
+  for (int r = 0; r < n; ++r)
+    m->rec_nodes[r] = node_id(m, ijk[3 * r], ijk[3 * r + 1], ijk[3 * r + 2]);
+  if (m->d_traces) cudaFree(m->d_traces);
+  m->d_traces = nullptr;
+  m->trace_cap = 0;
+  return rebuild_receivers(m);
+}
+
+static int ensure_trace_capacity(vfe_mesh *m, int64_t rows) {
+  if (m->n_rec == 0 || rows <= m->trace_cap) return VFE_OK;
+  int64_t cap = std::max<int64_t>(rows, std::max<int64_t>(2 * m->trace_cap, 1024));
+  double *p = nullptr;
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (cudaMalloc(&p, sizeof(double) * 3 * m->n_rec * cap) != cudaSuccess)
+    return fail(VFE_ENOMEM, "trace buffer of %lld rows", (long long)cap);
+  if (m->d_traces && m->trace_rows > 0)
+    CUDA_TRY(cudaMemcpy(p, m->d_traces, sizeof(double) * 3 * m->n_rec * m->trace_rows,
+                        cudaMemcpyDeviceToDevice));
+  if (m->d_traces) cudaFree(m->d_traces);
+  m->d_traces = p;
+  m->trace_cap = cap;
+  invalidate_graphs(m);
+  return VFE_OK;
+}
+
+int vfe_step(vfe_mesh *m, int n) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  if (n < 0) return fail(VFE_EINVAL, "n must be >= 0");
+  if (n == 0) return VFE_OK;
+  cudaSetDevice(m->device);
+  int rc = ensure_trace_capacity(m, m->trace_rows + n);
+  if (rc != VFE_OK) return rc;
+  int64_t done = 0;
+  std::vector<double> series;
+  while (done < n) {
+    const int64_t chunk = std::min<int64_t>(n - done, kSeriesChunk);
+    // source samples for steps [steps, steps + chunk); FP64 path folds amp in
+    // the prologue, the TC path folds dt^2/m there as well
+    series.assign(chunk, 0.0);
+    if (m->has_src)
+      for (int64_t s = 0; s < chunk; ++s) {
+        const double t = (double)(m->steps + s) * m->dt;
+        series[s] = (m->opt.path == VFE_PATH_TC ? m->amp : 1.0) * ricker(t, m->f0, m->t0);
+      }
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    CUDA_TRY(cudaMemcpy(m->d_series, series.data(), sizeof(double) * chunk,
+                        cudaMemcpyHostToDevice));
+    const int64_t base = m->steps;
+    int64_t *persist = m->opt.path == VFE_PATH_TC ? m->d_tcpersist + 3 : m->d_f64persist + 2;
+    CUDA_TRY(cudaMemcpy(persist, &base, sizeof(int64_t), cudaMemcpyHostToDevice));
+    int64_t left = chunk;
+    while (left >= 2) {
+      rc = ensure_graph(m, m->cur);
+      if (rc != VFE_OK) return rc;
+      CUDA_TRY(cudaGraphLaunch(m->graph[m->cur], m->stream));
+      left -= 2;
+      m->steps += 2;
+      if (m->n_rec) m->trace_rows += 2;
+    }
+    if (left == 1) {
+      rc = enqueue_step(m, m->cur);
+      if (rc != VFE_OK) return rc;
+      m->cur = 1 - m->cur;
+      m->steps += 1;
+      if (m->n_rec) m->trace_rows += 1;
+    }
+    done += chunk;
+  }
+  return VFE_OK;
+}
+
+int vfe_synchronize(vfe_mesh *m) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return check_status(m);
+}
+
+int vfe_get_traces(vfe_mesh *m, double *out, int64_t *n_steps_out) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  int rc = vfe_synchronize(m);
+  if (rc != VFE_OK) return rc;
+  if (n_steps_out) *n_steps_out = m->trace_rows;
+  if (out && m->n_rec && m->trace_rows)
+    CUDA_TRY(cudaMemcpy(out, m->d_traces, sizeof(double) * 3 * m->n_rec * m->trace_rows,
+                        cudaMemcpyDeviceToHost));
+  return VFE_OK;
+}
+
+int vfe_get_dt(vfe_mesh *m, double *dt) {
+  if (!m || !dt) return fail(VFE_EINVAL, "NULL argument");
+  *dt = m->dt;
+  return VFE_OK;
+}
+
+int vfe_get_sizes(vfe_mesh *m, int64_t *n_nodes, int64_t *n_elements) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  if (n_nodes) *n_nodes = m->nn;
+  if (n_elements) *n_elements = m->ne;
+  return VFE_OK;
+}
+
+int vfe_get_step_count(vfe_mesh *m, int64_t *steps) {
+  if (!m || !steps) return fail(VFE_EINVAL, "NULL argument");
+  *steps = m->steps;
+  return VFE_OK;
+}
+
+}  // extern "C"
+
+// ---- state conversion (FP64 <-> fixed point for the TC path) -----------------
+
+// F such that max|u| 2^F lies in [2^57, 2^58); 0 for an all-zero field
+static int pick_frac_bits(const double *a, const double *b, int64_t n) {
+  double mx = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    mx = std::max(mx, std::fabs(a[i]));
+    if (b) mx = std::max(mx, std::fabs(b[i]));
+  }
+  if (mx == 0.0) return 0;
+  return (TC_UNITS_BITS - 1) - std::ilogb(mx);
+}
+
+static void to_fixed(const vfe_mesh *m, const double *u, int F, std::vector<int64_t> &U,
+                     bool zero_fixed, unsigned long long *orv) {
+  U.assign(3 * m->comp, 0);
+  unsigned long long acc = 0;
+  for (int64_t n = 0; n < m->nn; ++n) {
+    if (zero_fixed && m->fixed[n]) continue;
+    const int64_t t = tc_index(m, n);
+    for (int c = 0; c < 3; ++c) {
+      const int64_t v = llrint(std::ldexp(u[3 * n + c], F));
+      U[c * m->comp + t] = v;
+      acc |= (unsigned long long)(v < 0 ? -v : v);
+    }
+  }
+  if (orv) *orv = acc;
+}
+
+static int bitlen(unsigned long long v) { return v ? 64 - __builtin_clzll(v) : 0; }
+
+extern "C" {
+
+int vfe_set_state(vfe_mesh *m, const double *u, const double *u_prev) {
+  if (!m || !u || !u_prev) return fail(VFE_EINVAL, "NULL argument");
+  for (int64_t i = 0; i < 3 * m->nn; ++i)
+    if (!std::isfinite(u[i]) || !std::isfinite(u_prev[i]))
+      return fail(VFE_EINVAL, "state has non-finite values");
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (m->opt.path == VFE_PATH_TC) {
+    const int F = pick_frac_bits(u, u_prev, 3 * m->nn);
+    std::vector<int64_t> U0, U1;
+    unsigned long long o0 = 0, o1 = 0;
+    to_fixed(m, u, F, U0, true, &o0);
+    to_fixed(m, u_prev, F, U1, true, &o1);
+    CUDA_TRY(cudaMemcpy(m->d_U[m->cur], U0.data(), sizeof(int64_t) * U0.size(),
+                        cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->d_U[1 - m->cur], U1.data(), sizeof(int64_t) * U1.size(),
+                        cudaMemcpyHostToDevice));
+    // the next prologue reads slot (step + 2) % 3 for the bit length of u^n
+    unsigned long long slots[3] = {0, 0, 0};
+    slots[(m->steps + 2) % 3] = o0 | o1;
+    CUDA_TRY(cudaMemcpy(m->d_or, slots, sizeof(slots), cudaMemcpyHostToDevice));
+    int64_t F64 = F, zero = 0;
+    CUDA_TRY(cudaMemcpy(m->d_tcpersist, &F64, sizeof(int64_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->d_tcpersist + 5, &zero, sizeof(int64_t), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<double> a(u, u + 3 * m->nn), b(u_prev, u_prev + 3 * m->nn);
+    for (int64_t n = 0; n < m->nn; ++n)
+      if (m->fixed[n])
+        for (int c = 0; c < 3; ++c) a[3 * n + c] = b[3 * n + c] = 0.0;
+    CUDA_TRY(cudaMemcpy(m->d_u[m->cur], a.data(), sizeof(double) * a.size(),
+                        cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->d_u[1 - m->cur], b.data(), sizeof(double) * b.size(),
+                        cudaMemcpyHostToDevice));
+  }
+  return VFE_OK;
+}
+
+int vfe_get_state(vfe_mesh *m, double *u, double *u_prev) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  int rc = vfe_synchronize(m);
+  if (rc != VFE_OK) return rc;
+  if (m->opt.path == VFE_PATH_TC) {
+    int64_t pers[8];
+    CUDA_TRY(cudaMemcpy(pers, m->d_tcpersist, sizeof(pers), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> U(3 * m->comp);
+    for (int which = 0; which < 2; ++which) {
+      double *dst = which == 0 ? u : u_prev;
+      if (!dst) continue;
+      // u^n is stored with F = pers[0], u^{n-1} with F + (shift of the last step)
+      const int64_t F = which == 0 ? pers[0] : pers[0] + pers[5];
+      CUDA_TRY(cudaMemcpy(U.data(), m->d_U[which == 0 ? m->cur : 1 - m->cur],
+                          sizeof(int64_t) * U.size(), cudaMemcpyDeviceToHost));
+      for (int64_t n = 0; n < m->nn; ++n) {
+        const int64_t t = tc_index(m, n);
+        for (int c = 0; c < 3; ++c) dst[3 * n + c] = std::ldexp((double)U[c * m->comp + t], -(int)F);
+      }
+    }
+  } else {
+    if (u)
+      CUDA_TRY(cudaMemcpy(u, m->d_u[m->cur], sizeof(double) * 3 * m->nn, cudaMemcpyDeviceToHost));
+    if (u_prev)
+      CUDA_TRY(cudaMemcpy(u_prev, m->d_u[1 - m->cur], sizeof(double) * 3 * m->nn,
+                          cudaMemcpyDeviceToHost));
+  }
+  return VFE_OK;
+}
+
+// K u through the kernels (mode 1: S output, mode 2: exact partials)
+static int tc_apply(vfe_mesh *m, const double *u, int mode, std::vector<int64_t> &out, int *shq_out,
+                    int *F_out) {
+  const int F = pick_frac_bits(u, nullptr, 3 * m->nn);
+  std::vector<int64_t> U;
+  unsigned long long orv = 0;
+  to_fixed(m, u, F, U, false, &orv);
+  const int shq = std::max(0, bitlen(orv) - TC_QBITS);
+  int64_t *dU = nullptr, *dout = nullptr;
+  TcStepParams *dp = nullptr;
+  const size_t ubytes = sizeof(int64_t) * U.size();
+  const size_t obytes = mode == TC_MODE_KU ? ubytes : sizeof(int64_t) * 48 * m->ne;
+  int rc = VFE_OK;
+  cudaError_t e;
+  do {
+    if ((e = cudaMalloc(&dU, ubytes)) != cudaSuccess || (e = cudaMalloc(&dout, obytes)) != cudaSuccess ||
+        (e = cudaMalloc(&dp, sizeof(TcStepParams))) != cudaSuccess) {
+      rc = fail(VFE_ENOMEM, "scratch allocation: %s", cudaGetErrorString(e));
+      break;
+    }
+    TcStepParams p;
+    memset(&p, 0, sizeof(p));
+    p.trace_row = -1;
+    p.shq = shq;
+    p.F = F;
+    if ((e = cudaMemcpy(dU, U.data(), ubytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(dout, 0, obytes)) != cudaSuccess ||
+        (e = cudaMemcpy(dp, &p, sizeof(p), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "upload: %s", cudaGetErrorString(e));
+      break;
+    }
+    // a tensor map over the scratch copy of u
+    CUtensorMap tm;
+    cuuint64_t dims[4] = {(cuuint64_t)m->nxp, (cuuint64_t)m->nyp, (cuuint64_t)(m->nz + 1), 3};
+    cuuint64_t strides[3] = {(cuuint64_t)m->nxp * 8, (cuuint64_t)m->plane * 8,
+                             (cuuint64_t)m->comp * 8};
+    cuuint32_t box[4] = {TC_BOXX, TC_NODES, 1, 3};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = encode_fn()(&tm, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, dU, dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { rc = fail(VFE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r); break; }
+    TcDevice d = tc_device(m, m->cur);
+    d.params = dp;
+    d.src_node = -1;
+    d.n_rec = 0;
+    d.S_out = mode == TC_MODE_KU ? dout : nullptr;
+    d.partials_out = mode == TC_MODE_PARTIALS ? dout : nullptr;
+    if ((e = tc_launch_step(m->stream, d, &tm, mode)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "K u kernel: %s", cudaGetErrorString(e));
+      break;
+    }
+    rc = check_status(m);
+    if (rc != VFE_OK) break;
+    out.resize(obytes / sizeof(int64_t));
+    if ((e = cudaMemcpy(out.data(), dout, obytes, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "download: %s", cudaGetErrorString(e));
+      break;
+    }
+  } while (0);
+  if (dU) cudaFree(dU);
+  if (dout) cudaFree(dout);
+  if (dp) cudaFree(dp);
+  *shq_out = shq;
+  *F_out = F;
+  return rc;
+}
+
+int vfe_internal_force(vfe_mesh *m, const double *u, double *f) {
+  if (!m || !u || !f) return fail(VFE_EINVAL, "NULL argument");
+  for (int64_t i = 0; i < 3 * m->nn; ++i)
+    if (!std::isfinite(u[i])) return fail(VFE_EINVAL, "u has non-finite values");
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (m->opt.path == VFE_PATH_TC) {
+    std::vector<int64_t> S;
+    int shq = 0, F = 0;
+    int rc = tc_apply(m, u, TC_MODE_KU, S, &shq, &F);
+    if (rc != VFE_OK) return rc;
+    const int ex = 64 - m->e_ref + shq - F;
+    for (int64_t n = 0; n < m->nn; ++n) {
+      const int64_t t = tc_index(m, n);
+      for (int c = 0; c < 3; ++c) f[3 * n + c] = std::ldexp((double)S[c * m->comp + t], ex);
+    }
+    return VFE_OK;
+  }
+  double *du = nullptr, *df = nullptr;
+  int rc = VFE_OK;
+  cudaError_t e;
+  do {
+    if ((e = cudaMalloc(&du, sizeof(double) * 3 * m->nn)) != cudaSuccess ||
+        (e = cudaMalloc(&df, sizeof(double) * 3 * m->nn)) != cudaSuccess) {
+      rc = fail(VFE_ENOMEM, "scratch allocation: %s", cudaGetErrorString(e));
+      break;
+    }
+    if ((e = cudaMemcpy(du, u, sizeof(double) * 3 * m->nn, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "upload: %s", cudaGetErrorString(e));
+      break;
+    }
+    F64Device d = f64_device(m, m->cur);
+    d.u = du;
+    d.f_out = df;
+    if ((e = f64_launch_step(m->stream, d, m->d_f64params, 1)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(m->stream)) != cudaSuccess ||
+        (e = cudaMemcpy(f, df, sizeof(double) * 3 * m->nn, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "K u kernel: %s", cudaGetErrorString(e));
+      break;
+    }
+  } while (0);
+  if (du) cudaFree(du);
+  if (df) cudaFree(df);
+  return rc;
+}
+
+int vfe_debug_tc_partials(vfe_mesh *m, const double *u, int n, const int64_t *ids, int64_t *out,
+                          int *shift_out, int *frac_bits_out) {
+  if (!m || !u || (n > 0 && (!ids || !out))) return fail(VFE_EINVAL, "NULL argument");
+  if (m->opt.path != VFE_PATH_TC) return fail(VFE_ESTATE, "mesh is not on the tensor-core path");
+  for (int q = 0; q < n; ++q)
+    if (ids[q] < 0 || ids[q] >= m->ne) return fail(VFE_EINVAL, "element id %lld out of range",
+                                                   (long long)ids[q]);
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  std::vector<int64_t> all;
+  int shq = 0, F = 0;
+  int rc = tc_apply(m, u, TC_MODE_PARTIALS, all, &shq, &F);
+  if (rc != VFE_OK) return rc;
+  for (int q = 0; q < n; ++q) memcpy(out + 48 * q, all.data() + 48 * ids[q], 48 * sizeof(int64_t));
+  if (shift_out) *shift_out = shq;
+  if (frac_bits_out) *frac_bits_out = F;
+  return VFE_OK;
+}
+
+}  // extern "C"

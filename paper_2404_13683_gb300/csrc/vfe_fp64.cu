@@ -1,0 +1,120 @@
+// vfe_fp64.cu -- the plain FP64 CUDA-core path (baseline form).
+//
+// f = K u element by element in FP64 with the per-material 24x24 element
+// matrices (Section 2: VFEM or OVFEM, Eq. OVFEMstiff), followed by the
+// central-difference update with the diagonal mass (Eq. eqtimehistory).
+// One thread per node gathers the rows of its (up to) eight elements, so the
+// node sums need no atomics and the update is fused into the same pass.
+// The path is FP64-bound (576 FMA per node), which is the point: it is the
+// baseline the integer tensor-core path is measured against.
+#include "vfe_internal.h"
+
+struct F64StepParams {
+  int64_t step;
+  int64_t trace_row;
+  double src[3];
+};
+
+// persist[0] = step, [1] = trace rows, [2] = series base
+__global__ void f64_prologue_kernel(F64StepParams *p, int64_t *persist, const double *series,
+                                    double d0, double d1, double d2, int have_src, int trace_on) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int64_t n = persist[0];
+  F64StepParams q;
+  q.step = n;
+  q.trace_row = trace_on ? persist[1] : -1;
+  const double fv = have_src ? series[n - persist[2]] : 0.0;
+  q.src[0] = fv * d0;
+  q.src[1] = fv * d1;
+  q.src[2] = fv * d2;
+  *p = q;
+  persist[0] = n + 1;
+  if (trace_on) persist[1] += 1;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) f64_step_kernel(const F64Device d, const F64StepParams *pp) {
+  extern __shared__ double sK[];
+  for (int i = threadIdx.x; i < d.n_mat * 576; i += blockDim.x) sK[i] = d.K[i];
+  __syncthreads();
+  const int nx = d.nx, ny = d.ny, nz = d.nz;
+  const int64_t sx = nx + 1, sxy = (int64_t)(nx + 1) * (ny + 1);
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < d.nn;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    const int ni = (int)(n % sx), nj = (int)((n / sx) % (ny + 1)), nk = (int)(n / sxy);
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    for (int a = 0; a < 8; ++a) {
+      const int ex = ni - (a & 1), ey = nj - ((a >> 1) & 1), ez = nk - (a >> 2);
+      if (ex < 0 || ey < 0 || ez < 0 || ex >= nx || ey >= ny || ez >= nz) continue;
+      const int m = d.mat[(int64_t)ex + (int64_t)nx * ((int64_t)ey + (int64_t)ny * ez)];
+      if (m < 0) continue;
+      const double *K = sK + m * 576 + (3 * a) * 24;
+      for (int b = 0; b < 8; ++b) {
+        const int64_t nb = (ex + (b & 1)) + sx * (ey + ((b >> 1) & 1)) + sxy * (ez + (b >> 2));
+        const double u0 = d.u[3 * nb], u1 = d.u[3 * nb + 1], u2 = d.u[3 * nb + 2];
+        const double *k0 = K + 3 * b, *k1 = K + 24 + 3 * b, *k2 = K + 48 + 3 * b;
+        f0 = fma(k0[0], u0, fma(k0[1], u1, fma(k0[2], u2, f0)));
+        f1 = fma(k1[0], u0, fma(k1[1], u1, fma(k1[2], u2, f1)));
+        f2 = fma(k2[0], u0, fma(k2[1], u1, fma(k2[2], u2, f2)));
+      }
+    }
+    if (MODE == 1) {
+      d.f_out[3 * n] = f0;
+      d.f_out[3 * n + 1] = f1;
+      d.f_out[3 * n + 2] = f2;
+      continue;
+    }
+    const F64StepParams p = *pp;
+    const double c = d.dt2_m[n];
+    const bool src = (n == d.src_node);
+    const double fv[3] = {f0, f1, f2};
+    double un[3];
+    for (int k = 0; k < 3; ++k) {
+      const double F = src ? p.src[k] : 0.0;
+      un[k] = c == 0.0 ? 0.0 : 2.0 * d.u[3 * n + k] - d.u_prev[3 * n + k] + c * (F - fv[k]);
+      d.u_next[3 * n + k] = un[k];
+    }
+    if (p.trace_row >= 0) {
+      for (int r = 0; r < d.n_rec; ++r)
+        if (d.recv_nodes[r] == n)
+          for (int k = 0; k < 3; ++k) d.traces[(p.trace_row * d.n_rec + r) * 3 + k] = un[k];
+    }
+  }
+}
+
+cudaError_t f64_prepare() {
+  const int smem = F64_MAX_MAT * 576 * (int)sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(f64_step_kernel<0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(f64_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem);
+}
+
+template <int MODE>
+static cudaError_t f64_launch(cudaStream_t s, const F64Device &d, const F64StepParams *pp) {
+  const int smem = d.n_mat * 576 * (int)sizeof(double);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t blocks = (d.nn + 255) / 256;
+  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  if (blocks < 1) blocks = 1;
+  f64_step_kernel<MODE><<<(unsigned)blocks, 256, smem, s>>>(d, pp);
+  return cudaGetLastError();
+}
+
+size_t f64_params_bytes() { return sizeof(F64StepParams); }
+
+cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,
+                                const double *series, const double dir[3], int have_src,
+                                int trace_on) {
+  f64_prologue_kernel<<<1, 32, 0, s>>>(reinterpret_cast<F64StepParams *>(params), persist, series,
+                                       dir[0], dir[1], dir[2], have_src, trace_on);
+  return cudaGetLastError();
+}
+
+cudaError_t f64_launch_step(cudaStream_t s, const F64Device &d, const void *params, int mode) {
+  const F64StepParams *pp = reinterpret_cast<const F64StepParams *>(params);
+  return mode == 1 ? f64_launch<1>(s, d, pp) : f64_launch<0>(s, d, pp);
+}

@@ -1,0 +1,119 @@
+// vfe_internal.h -- structures shared by the host code and the kernels of the
+// GB300 voxel FE wave solver.  Not part of the public ABI (see include/vfe.h).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vfe.h"
+
+// ----------------------------------------------------------------------------
+// TC path geometry.  A CTA owns a column of TC_OWN x TC_OWN nodes in x-y and a
+// chunk of node planes in z, and computes the (TC_OWN+1)^2 = 256 elements per
+// layer that touch its nodes (one element of halo on the low x and y sides).
+// The 256 elements form two MMA tiles of M = 128 rows.
+// ----------------------------------------------------------------------------
+#define TC_EX 16                 // elements per layer tile in x and in y
+#define TC_OWN (TC_EX - 1)       // owned nodes per tile in x and in y
+#define TC_NODES (TC_EX + 1)     // node rows/columns touched by the tile
+#define TC_BOXX 18               // TMA box width in x (int64; 144 B)
+#define TC_MAX_STAGES 5          // 11-bit digit stages (5 x 11 = 55 bits)
+#define TC_DIGIT_BITS 11
+#define TC_QBITS 52              // |q| < 2^52 after the per-step shift
+#define TC_N 48                  // MMA N: 24 K^kappa rows + 24 K^G' rows
+#define TC_THREADS 256
+#define TC_MAX_MAT 64            // materials per mesh on the TC path
+#define TC_MAX_REC_CTA 64        // receivers handled per CTA work item
+#define TC_UNITS_BITS 58         // target bit length of max |U| after rescale
+
+// fp32 magic bias: 8 padding K-rows carry A = 128, B = 12288 so that every
+// accumulator starts from 1.5 * 2^23; its bit pattern is then 0x4B400000 + d
+// for the exact integer d (|d| < 2^22).
+#define TC_MAGIC_A 128.0f
+#define TC_MAGIC_B 12288.0f
+#define TC_MAGIC_BITS 0x4B400000
+
+struct TcStepParams {     // written by the per-step prologue kernel
+  int64_t step;           // global step index n (source time n*dt)
+  int64_t trace_row;      // row of the trace buffer for this step (-1: none)
+  int64_t dU_src[3];      // source increment in the new fixed-point units
+  int rs;                 // rescale: U_new units = old units * 2^rs
+  int shq;                // digit shift: q = U_raw >> shq
+  int R;                  // right shift of S*C (128-bit) giving dU
+  int F;                  // fraction bits after this step (u = U * 2^-F)
+  int or_slot;            // slot this step ORs |U_new| into
+  int rs_prev;            // shift of the previous step: u^{n-1} is stored in
+                          // units 2^-(F_old + rs_prev)
+};
+
+struct TcMaterial {       // per-material integer multipliers
+  int64_t A;              // round(kappa ds/256 * 2^e), <= 2^60
+  int64_t B;              // round(G ds/384 * 2^e)
+  int shift;              // e - e_ref (>= 0): right shift to the common unit
+  int pad;
+};
+
+struct TcRecv {           // receiver handled by a CTA work item
+  int16_t ei, ej;         // owning thread's element coordinates in the tile
+  int32_t k;              // node plane
+  int32_t r;              // receiver index
+  int32_t pad;
+};
+
+struct TcDevice {         // everything the TC kernels read (by value)
+  int nx, ny, nz, nxp;    // nxp: padded x pitch of nodal arrays (multiple of 4)
+  int tiles_x, tiles_y, tiles_z, cz;  // work decomposition; cz planes per chunk
+  int n_mat, stages, n_rec;
+  int64_t plane;          // nxp*(ny+1): nodal plane stride
+  int64_t comp;           // plane*(nz+1): component stride
+  const int32_t *mat;     // element material ids (x fastest)
+  const int64_t *C;       // per-node update multiplier round(dt^2/m 2^eC)
+  const int64_t *U_prev;  // u^{n-1} (also receives u^{n+1})
+  int64_t *U_next;        // same buffer as U_prev
+  const uint16_t *Bop;    // B operand image (fp16 bits), 48x32, core-matrix order
+  const TcMaterial *mats;
+  const TcRecv *recv;     // receivers, grouped per work item
+  const int32_t *recv_off;// work item -> first receiver, size items+1
+  int64_t src_node;       // -1: none
+  double *traces;         // [rows][n_rec][3]
+  unsigned long long *or_slots;  // 3 slots of OR(|U_new|)
+  int *status;            // device error flags (bit 0: wait timeout)
+  const TcStepParams *params;
+  int64_t *S_out;         // K u mode: per-node S (int64 x 3, SoA like U)
+  int64_t *partials_out;  // partials mode: per element 48 int64 (element order)
+};
+
+// FP64 path ------------------------------------------------------------------
+#define F64_MAX_MAT 24    // element matrices kept in shared memory
+
+struct F64Device {
+  int nx, ny, nz, n_mat, n_rec;
+  int64_t nn;
+  const int32_t *mat;
+  const double *K;        // n_mat * 576 element matrices
+  const double *u;        // u^n [nn][3]
+  const double *u_prev;   // u^{n-1}
+  double *u_next;         // u^{n+1}
+  const double *dt2_m;    // dt^2 / m per node, 0 for fixed / massless nodes
+  const int64_t *recv_nodes;
+  double *traces;
+  int64_t src_node;
+  double *f_out;          // K u mode output
+};
+
+// launch helpers implemented in the .cu files ---------------------------------
+enum { TC_MODE_STEP = 0, TC_MODE_KU = 1, TC_MODE_PARTIALS = 2 };
+int tc_smem_bytes();
+cudaError_t tc_prepare();
+cudaError_t f64_prepare();
+cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t *persist,
+                                  const double *series, unsigned long long *or_slots,
+                                  double src_scale, const double dir[3], int have_src,
+                                  int trace_on, int *status);
+cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
+
+size_t f64_params_bytes();
+cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,
+                                const double *series, const double dir[3], int have_src,
+                                int trace_on);
+cudaError_t f64_launch_step(cudaStream_t s, const F64Device &d, const void *params, int mode);

@@ -1,0 +1,660 @@
+// vfe_tc.cu -- OVFEM K u and central-difference step on GB300 tensor cores.
+//
+// Method (arXiv 2404.13683, Section 2, Eq. GE:TC and Eqs. intscaling,
+// int8comp1, int8comp2): the element product is split so that the tensor core
+// only ever multiplies small integers, and the partial products are
+// recombined exactly.  GB300 (sm_103a) has no tcgen05 kind::i8, so the
+// integer digits are carried exactly in fp16 (|digit| <= 1024, base 2^11) on
+// tcgen05.mma kind::f16 with fp32 accumulation; every partial sum stays below
+// 2^22 in magnitude, so the fp32 accumulator holds it exactly.
+//
+//   * The per-material integer matrices are K^kappa = 256/ds K_e(kappa=1,G=0)
+//     and K^G' = Kbar^G + 128 I = 384/ds K_e(kappa=0,G=1); stacking them as
+//     48 outputs of one MMA gives P = K^kappa q_e and Q = K^G' q_e, and
+//     K_e u_e = ds (kappa/256 P + G/384 Q) (Eq. GE:TC with the kappa and G
+//     parts kept separate, so the digits are per node, not per element).
+//   * Scaling (Eq. intscaling): one power-of-two shift per step puts every
+//     node value below 2^52 (q = floor(U / 2^shq)).
+//   * Hierarchical split (Eq. int8comp1): q = sum_s 2^(11 s) d_s with balanced
+//     digits d_s in [-1024, 1023] (offset-binary extraction), fp16-exact.
+//   * Recombination (Eq. int8comp2): sum_s 2^(11 s) D_s in int64.
+//
+// The state is a 64-bit fixed-point value u = U * 2^-F with a power-of-two
+// scale F that a one-thread prologue adjusts every step (FP64 is ~40x slower
+// than INT32 on GB300, so the per-element arithmetic is integer end to end).
+//
+// Tiling: a CTA owns 15 x 15 node columns in x-y and a chunk of node planes in
+// z, computes the 16 x 16 elements per layer that touch them (one element of
+// halo), and marches up in z.  Per layer: TMA brings the next node plane into
+// shared memory, threads digitise it into the MN-major operand layout the
+// tensor core reads directly (no im2col), one thread issues 2 tiles x stages x
+// 2 MMAs (M=128, N=48, K=16), the 256 threads read their element's 48 x
+// stages accumulators from TMEM, recombine, apply the element's material,
+// reduce to nodes (warp shuffle in x, shared memory in y, registers in z) and
+// update their node.
+#include <cuda_fp16.h>
+
+#include "vfe_internal.h"
+
+namespace {
+
+// --------------------------------------------------------------------------
+// shared-memory map (bytes)
+// --------------------------------------------------------------------------
+constexpr int kBlockBytes = 128;                          // one 8x8 fp16 core matrix
+constexpr int kStageBytes = TC_NODES * 2 * kBlockBytes;   // 17 rows x 2 x-chunks
+constexpr int kDigitSlotBytes = TC_MAX_STAGES * kStageBytes;
+constexpr int kDigitSlots = 3;
+constexpr int kUSlotBytes = 3 * TC_NODES * TC_BOXX * 8;   // TMA box (18,17,1,3) int64
+constexpr int kUSlotStride = (kUSlotBytes + 127) / 128 * 128;  // TMA smem dst: 128-B aligned
+constexpr int kUSlots = 4;
+constexpr int kBopBytes = TC_N * 32 * 2;
+constexpr int kYbufBytes = 2 * TC_EX * TC_EX * 3 * 8;
+
+constexpr int kOffDigits = 0;
+constexpr int kOffU = kOffDigits + kDigitSlots * kDigitSlotBytes;
+constexpr int kOffBop = kOffU + kUSlots * kUSlotStride;
+constexpr int kOffYbuf = kOffBop + kBopBytes;
+constexpr int kOffMat = kOffYbuf + kYbufBytes;
+constexpr int kOffRecv = kOffMat + TC_MAX_MAT * (int)sizeof(TcMaterial);
+constexpr int kOffBar = kOffRecv + TC_MAX_REC_CTA * (int)sizeof(TcRecv);
+constexpr int kOffMisc = kOffBar + 8 * 8;
+constexpr int kSmemUsed = kOffMisc + 64;
+// padded so that only one CTA fits per SM (it allocates 512 TMEM columns)
+constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
+
+static_assert(kOffU % 128 == 0 && kUSlotStride % 128 == 0, "TMA destinations are 128-byte aligned");
+static_assert(kDigitSlotBytes % 128 == 0 && kStageBytes % 128 == 0, "operand blocks 128-byte aligned");
+static_assert(kOffBop % 16 == 0 && kOffYbuf % 16 == 0 && kOffBar % 8 == 0, "alignment");
+static_assert(kSmemUsed <= 227 * 1024, "shared memory budget");
+
+constexpr int kTmemCols = 512;
+constexpr int kTileCols = TC_MAX_STAGES * TC_N;            // 240 columns per M tile
+
+// instruction descriptor, kind::f16: D f32, A f16 MN-major, B f16 K-major,
+// N = 48, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (0u << 16) |
+                            ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits give up after ~2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_u(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                           int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(0)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; no swizzle, base offset 0
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t &a, uint32_t &b, uint32_t &c,
+                                         uint32_t &d) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// floor(v / 2^s) for s >= 0, v * 2^-s for s < 0.  Left shifts only occur
+// when the prologue has checked that the result fits (|v| 2^-s < 2^59).
+__device__ __forceinline__ int64_t shr_floor(int64_t v, int s) {
+  if (s >= 0) return v >> min(s, 63);
+  return (int64_t)((uint64_t)v << min(-s, 63));
+}
+// round(v / 2^s), halves toward +inf, for |v| < 2^62; v * 2^-s for s <= 0
+__device__ __forceinline__ int64_t shr_round(int64_t v, int s) {
+  if (s <= 0) return (int64_t)((uint64_t)v << min(-s, 63));
+  if (s >= 63) return 0;
+  return (v + ((int64_t)1 << (s - 1))) >> s;
+}
+
+// exact small integer -> fp32 (|d| < 2^22) without a conversion instruction
+__device__ __forceinline__ float int_to_f32_exact(int d) {
+  return __int_as_float(TC_MAGIC_BITS + d) - 12582912.0f;
+}
+
+// exact integer from a magic-biased fp32 accumulator word
+__device__ __forceinline__ int acc_to_int(uint32_t w) { return (int)w - TC_MAGIC_BITS; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The fused kernel.  MODE: 0 = time step, 1 = K u only (writes S), 2 = exact
+// partial products per element (diagnostic).
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_step_kernel(const __grid_constant__ CUtensorMap tmap_u, const TcDevice d) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *digits = smem + kOffDigits;
+  int64_t *uslot = reinterpret_cast<int64_t *>(smem + kOffU);
+  uint16_t *bop = reinterpret_cast<uint16_t *>(smem + kOffBop);
+  int64_t *ybuf = reinterpret_cast<int64_t *>(smem + kOffYbuf);
+  TcMaterial *smat = reinterpret_cast<TcMaterial *>(smem + kOffMat);
+  TcRecv *srecv = reinterpret_cast<TcRecv *>(smem + kOffRecv);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..3: U slots, 4: MMA
+  uint32_t *misc = reinterpret_cast<uint32_t *>(smem + kOffMisc);  // [0] tmem base, [1] abort
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int item = blockIdx.x;
+  const int tx = item % d.tiles_x;
+  const int ty = (item / d.tiles_x) % d.tiles_y;
+  const int tz = item / (d.tiles_x * d.tiles_y);
+  const int X0 = TC_OWN * tx - 1;  // global x of local element/node column 0
+  const int Y0 = TC_OWN * ty - 1;
+  const int Z0 = tz * d.cz;
+  const int Z1 = min(Z0 + d.cz, d.nz + 1);  // owned node planes [Z0, Z1)
+  const int xbox = X0 & ~1;                 // TMA x must be even (16-byte rule)
+  const int xo = X0 - xbox;                 // 0 or 1: local node ni sits at box x = ni + xo
+
+  const TcStepParams P = *d.params;
+  // with fewer stages the low digits are dropped (the top ones carry the value)
+  const int s_lo = TC_MAX_STAGES - d.stages;
+
+  // thread <-> element: TMEM lane m of tile t holds element (m % 16, 8 t + m / 16)
+  const int tile = warp >> 2;
+  const int m_row = ((warp & 3) << 5) + lane;
+  const int ei = m_row & 15;
+  const int ej = 8 * tile + (m_row >> 4);
+  const int gi = X0 + ei + 1, gj = Y0 + ej + 1;  // this thread's node (ei+1, ej+1)
+  const bool own_xy = (ei < TC_OWN) && (ej < TC_OWN) && gi <= d.nx && gj <= d.ny;
+
+  // ---- one-time setup ------------------------------------------------------
+  if (tid == 0) {
+    misc[1] = 0;
+    for (int i = 0; i < kUSlots; ++i) mbar_init(&bars[i], 1);
+    mbar_init(&bars[4], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&misc[0])),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // B operand image and material table
+  for (int i = tid; i < kBopBytes / 16; i += TC_THREADS)
+    reinterpret_cast<uint4 *>(bop)[i] = reinterpret_cast<const uint4 *>(d.Bop)[i];
+  for (int i = tid; i < d.n_mat; i += TC_THREADS) smat[i] = d.mats[i];
+  // receivers of this work item
+  int rbeg = 0, nrec = 0;
+  if (MODE == TC_MODE_STEP && d.n_rec > 0 && P.trace_row >= 0) {
+    rbeg = d.recv_off[item];
+    nrec = min(d.recv_off[item + 1] - rbeg, TC_MAX_REC_CTA);
+    for (int i = tid; i < nrec; i += TC_THREADS) srecv[i] = d.recv[rbeg + i];
+  }
+  // magic rows (lines 6 and 7 of every block) of every digit slot and stage
+  {
+    const uint32_t mg = (uint32_t)__half_as_ushort(__float2half(TC_MAGIC_A));
+    const uint4 mv = make_uint4(mg | (mg << 16), mg | (mg << 16), mg | (mg << 16), mg | (mg << 16));
+    const int nblocks = kDigitSlots * TC_MAX_STAGES * TC_NODES * 2;
+    for (int i = tid; i < 2 * nblocks; i += TC_THREADS) {
+      int blk = i >> 1, line = 6 + (i & 1);
+      *reinterpret_cast<uint4 *>(digits + blk * kBlockBytes + line * 16) = mv;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = misc[0];
+
+  uint32_t uphase = 0;    // parity bit per U slot
+  uint32_t mma_phase = 0;
+  bool aborted = false;
+
+  auto issue_plane = [&](int p) {  // TMA of node plane p into U slot p & 3
+    if (tid == 0) {
+      int s = p & 3;
+      mbar_expect_tx(&bars[s], kUSlotBytes);
+      tma_load_u(uslot + s * (kUSlotStride / 8), &tmap_u, &bars[s], xbox, Y0, p);
+    }
+  };
+  // all threads wait for plane p; returns false on timeout
+  auto wait_plane = [&](int p) -> bool {
+    int s = p & 3;
+    bool ok = mbar_wait(&bars[s], (uphase >> s) & 1u);
+    uphase ^= 1u << s;
+    return ok;
+  };
+  // digitise node plane p into digit slot p mod 3 (threads 0..101)
+  auto digitise = [&](int p) {
+    if (tid < TC_NODES * 6) {
+      const int nj = tid / 6, r = tid % 6, xc = r / 3, c = r % 3;
+      const int64_t *src = uslot + (p & 3) * (kUSlotStride / 8) + (c * TC_NODES + nj) * TC_BOXX +
+                           8 * xc + xo;
+      // offset-binary bias sum_s 1024 * 2^(11 s) over the 5 digit positions
+      const int64_t boff = (1LL << 10) | (1LL << 21) | (1LL << 32) | (1LL << 43) | (1LL << 54);
+      int64_t v[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) v[i] = shr_floor(src[i], P.shq) + boff;
+      unsigned char *slot = digits + ((p % kDigitSlots + kDigitSlots) % kDigitSlots) * kDigitSlotBytes;
+      for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
+        float f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          f[i] = int_to_f32_exact((int)((v[i] >> (TC_DIGIT_BITS * s)) & 2047) - 1024);
+        uint4 lo, hi;  // dx = 0 line: nodes 0..7, dx = 1 line: nodes 1..8
+        __half2 h;
+        h = __floats2half2_rn(f[0], f[1]); lo.x = *reinterpret_cast<uint32_t *>(&h);
+        h = __floats2half2_rn(f[2], f[3]); lo.y = *reinterpret_cast<uint32_t *>(&h);
+        h = __floats2half2_rn(f[4], f[5]); lo.z = *reinterpret_cast<uint32_t *>(&h);
+        h = __floats2half2_rn(f[6], f[7]); lo.w = *reinterpret_cast<uint32_t *>(&h);
+        h = __floats2half2_rn(f[1], f[2]); hi.x = *reinterpret_cast<uint32_t *>(&h);
+        h = __floats2half2_rn(f[3], f[4]); hi.y = *reinterpret_cast<uint32_t *>(&h);
+        h = __floats2half2_rn(f[5], f[6]); hi.z = *reinterpret_cast<uint32_t *>(&h);
+        h = __floats2half2_rn(f[7], f[8]); hi.w = *reinterpret_cast<uint32_t *>(&h);
+        unsigned char *blk = slot + s * kStageBytes + (nj * 2 + xc) * kBlockBytes;
+        *reinterpret_cast<uint4 *>(blk + c * 16) = lo;
+        *reinterpret_cast<uint4 *>(blk + (3 + c) * 16) = hi;
+      }
+    }
+  };
+  // one thread issues the MMAs of element layer L (node planes L, L+1)
+  auto issue_mma = [&](int L) {
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t bbase = smem_u32(bop);
+      for (int t = 0; t < 2; ++t)
+        for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
+          const uint32_t dcol = tmem_base + (uint32_t)(t * kTileCols + s * TC_N);
+          for (int dz = 0; dz < 2; ++dz) {
+            const int p = L + dz;
+            const int slot = ((p % kDigitSlots) + kDigitSlots) % kDigitSlots;
+            const uint32_t abase = smem_u32(digits + slot * kDigitSlotBytes + s * kStageBytes +
+                                            (16 * t) * kBlockBytes);
+            // A (MN-major): 8-element chunks at 128 B, K groups (dy) at 256 B
+            const uint64_t adesc = make_sdesc(abase, 2 * kBlockBytes, kBlockBytes);
+            // B (K-major): 8-row N groups at 128 B, K groups at 6*128 B
+            const uint64_t bdesc = make_sdesc(bbase + dz * 2 * 6 * kBlockBytes, 6 * kBlockBytes,
+                                              kBlockBytes);
+            mma_f16(dcol, adesc, bdesc, dz);
+          }
+        }
+      mma_commit(&bars[4]);
+    }
+  };
+  auto sync_abort = [&](bool ok) -> bool {  // true if the CTA must stop
+    if (!ok) atomicExch(&misc[1], 1u);
+    __syncthreads();
+    return misc[1] != 0;
+  };
+
+  // ---- prologue: planes Z0-1, Z0, Z0+1 ------------------------------------
+  const int Lfirst = Z0 - 1, Llast = Z1 - 1;
+  issue_plane(Lfirst);
+  issue_plane(Lfirst + 1);
+  issue_plane(Lfirst + 2);
+  bool ok = wait_plane(Lfirst);
+  ok = wait_plane(Lfirst + 1) && ok;
+  aborted = sync_abort(ok);
+  if (!aborted) {
+    digitise(Lfirst);
+    digitise(Lfirst + 1);
+    fence_async_smem();
+    __syncthreads();
+    issue_mma(Lfirst);
+  }
+
+  // per-thread running state
+  int64_t carry[3] = {0, 0, 0};          // forces on (ei+1, ej+1) at plane L from layer L-1
+  unsigned long long or_acc = 0;
+  const TcMaterial zero_mat = {0, 0, 0, 0};
+
+  for (int L = Lfirst; L <= Llast && !aborted; ++L) {
+    // element material for this layer (void outside the mesh)
+    const int gx = X0 + ei, gy = Y0 + ej;
+    int m = -1;
+    if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && L >= 0 && L < d.nz)
+      m = d.mat[(int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L)];
+    // update operands of plane L (prefetched before the epilogue)
+    int64_t uprev[3] = {0, 0, 0}, cn = 0;
+    const bool upd = (MODE == TC_MODE_STEP) && own_xy && L >= Z0;
+    const int64_t nidx = (int64_t)L * d.plane + (int64_t)gj * d.nxp + gi;
+    if (upd) {
+      cn = d.C[nidx];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) uprev[c] = d.U_prev[c * d.comp + nidx];
+    }
+
+    // (a) digitise plane L+2 while MMA(L) runs; prefetch plane L+3
+    bool okp = true;
+    if (L + 2 <= Llast + 1) {
+      okp = wait_plane(L + 2);
+    }
+    if (sync_abort(okp)) { aborted = true; break; }
+    if (L + 2 <= Llast + 1) digitise(L + 2);
+    if (L + 3 <= Llast + 1) issue_plane(L + 3);
+
+    // (b) wait for MMA(L)
+    bool okm = mbar_wait(&bars[4], mma_phase);
+    mma_phase ^= 1u;
+    if (sync_abort(okm)) { aborted = true; break; }
+    tc_fence_after();
+
+    // (c) epilogue: per corner group (dy, dz), 5 stages x 12 columns
+    const TcMaterial mt = m >= 0 ? smat[m] : zero_mat;
+    const uint32_t tbase =
+        tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * kTileCols);
+    int64_t accL[3] = {0, 0, 0}, carry_next[3] = {0, 0, 0};
+    int64_t *ybuf0 = ybuf, *ybuf1 = ybuf + TC_EX * TC_EX * 3;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      int64_t pq[12];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) pq[i] = 0;
+      for (int s = TC_MAX_STAGES - 1; s >= s_lo; --s) {
+        uint32_t w[12];
+        const uint32_t ta = tbase + (uint32_t)(s * TC_N + 12 * g);
+        tmem_ld4(ta + 0, w[0], w[1], w[2], w[3]);
+        tmem_ld4(ta + 4, w[4], w[5], w[6], w[7]);
+        tmem_ld4(ta + 8, w[8], w[9], w[10], w[11]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 12; ++i) pq[i] = pq[i] * 2048 + (int64_t)acc_to_int(w[i]);
+      }
+      if (s_lo > 0) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) pq[i] *= (int64_t)1 << (TC_DIGIT_BITS * s_lo);
+      }
+      if (MODE == TC_MODE_PARTIALS) {
+        if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && L >= 0 && L < d.nz) {
+          const int64_t e = (int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L);
+          const int dy = g & 1, dz = g >> 1;
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const int a = dx + 2 * dy + 4 * dz;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              d.partials_out[e * 48 + 3 * a + c] = pq[6 * dx + c];
+              d.partials_out[e * 48 + 24 + 3 * a + c] = pq[6 * dx + 3 + c];
+            }
+          }
+        }
+        continue;
+      }
+      // material: t = (P A + Q B) / 2^64, then to the common unit
+      int64_t f0[3], f1[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        int64_t t0 = __mul64hi(pq[c], mt.A) + __mul64hi(pq[3 + c], mt.B);
+        int64_t t1 = __mul64hi(pq[6 + c], mt.A) + __mul64hi(pq[9 + c], mt.B);
+        f0[c] = shr_round(t0, mt.shift);
+        f1[c] = shr_round(t1, mt.shift);
+      }
+      // x reduction: node (ei+1) gets dx=1 of element ei and dx=0 of ei+1
+      int64_t v[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        int64_t nb = __shfl_down_sync(0xffffffffu, f0[c], 1);
+        v[c] = f1[c] + (ei < TC_EX - 1 ? nb : 0);
+      }
+      const int dy = g & 1, dz = g >> 1;
+      if (dy == 0) {
+        int64_t *yb = (dz == 0 ? ybuf0 : ybuf1) + (ej * TC_EX + ei) * 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) yb[c] = v[c];
+      } else if (dz == 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) accL[c] = v[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) carry_next[c] = v[c];
+      }
+    }
+    // (d) TMEM reads done; digit writes visible to the tensor core; issue MMA(L+1)
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+    if (L + 1 <= Llast) issue_mma(L + 1);
+    if (MODE == TC_MODE_PARTIALS) continue;
+
+    // (e) y reduction from the shared buffer, then the z carry
+    if (ej < TC_EX - 1) {
+      const int64_t *y0 = ybuf0 + ((ej + 1) * TC_EX + ei) * 3;
+      const int64_t *y1 = ybuf1 + ((ej + 1) * TC_EX + ei) * 3;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        accL[c] += y0[c];
+        carry_next[c] += y1[c];
+      }
+    }
+    int64_t S[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      S[c] = carry[c] + accL[c];
+      carry[c] = carry_next[c];
+    }
+
+    // (f) update / output of node (gi, gj, L)
+    if (own_xy && L >= Z0) {
+      if (MODE == TC_MODE_KU) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d.S_out[c * d.comp + nidx] = S[c];
+      } else if (MODE == TC_MODE_STEP) {
+        const int64_t *ucur = uslot + (L & 3) * (kUSlotStride / 8);
+        const bool is_src = (nidx == d.src_node);
+        int64_t unew[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int64_t u0 = shr_round(ucur[(c * TC_NODES + ej + 1) * TC_BOXX + ei + 1 + xo], P.rs);
+          const int64_t um = shr_round(uprev[c], P.rs + P.rs_prev);
+          const __int128 prod = (__int128)S[c] * (__int128)cn;
+          int64_t du;
+          if (P.R > 0) {
+            const int R = min(P.R, 126);
+            du = (int64_t)((prod + ((__int128)1 << (R - 1))) >> R);
+          } else {  // the state is being scaled up: exact left shift
+            du = (int64_t)(prod << min(-P.R, 63));
+          }
+          int64_t un = 2 * u0 - um - du;
+          if (is_src) un += P.dU_src[c];
+          if (cn == 0) un = 0;  // fixed or massless node
+          unew[c] = un;
+          d.U_next[c * d.comp + nidx] = un;
+          // the slot bounds u^{n+1} and u^n (both in the new units)
+          or_acc |= (unsigned long long)(un < 0 ? -un : un) | (unsigned long long)(u0 < 0 ? -u0 : u0);
+        }
+        for (int r = 0; r < nrec; ++r) {
+          const TcRecv rv = srecv[r];
+          if (rv.ei == ei && rv.ej == ej && rv.k == L) {
+            double *out = d.traces + (P.trace_row * d.n_rec + rv.r) * 3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[c] = ldexp((double)unew[c], -P.F);
+          }
+        }
+      }
+    }
+  }
+
+  // ---- teardown -------------------------------------------------------------
+  if (MODE == TC_MODE_STEP) {
+    for (int o = 16; o > 0; o >>= 1) or_acc |= __shfl_xor_sync(0xffffffffu, or_acc, o);
+    if (lane == 0 && or_acc) atomicOr(&d.or_slots[P.or_slot], or_acc);
+  }
+  if (aborted && tid == 0) atomicOr(d.status, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kTmemCols));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-step prologue: rescale decision, digit shift, source increment
+// ---------------------------------------------------------------------------
+// persist[0] = F of u^n, [1] = step, [2] = trace rows, [3] = series base,
+// [4] = eC + e_ref, [5] = shift of the last step (u^{n-1} has F + [5])
+__global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist,
+                                   const double *series, unsigned long long *or_slots,
+                                   double src_scale, double dir0, double dir1, double dir2,
+                                   int have_src, int trace_on, int *status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int64_t n = persist[1];
+  const int F_old = (int)persist[0];
+  const unsigned long long orp = or_slots[(n + 2) % 3];
+  // bit lengths of max|u^n|, max|u^{n-1}| (raw units) and of the source
+  // increment at the old scale; 'valid' flags separate zero from tiny
+  const int b = orp ? 64 - __clzll((long long)orp) : 0;
+  double src[3] = {0.0, 0.0, 0.0};
+  int bs = 0;
+  bool bs_valid = false;
+  if (have_src) {
+    const double fv = series[n - persist[3]] * src_scale;
+    const double dir[3] = {dir0, dir1, dir2};
+    double mx = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      src[c] = fv * dir[c];
+      mx = fmax(mx, fabs(src[c]));
+    }
+    if (mx > 0.0) {
+      bs = ilogb(mx) + F_old + 1;
+      bs_valid = true;
+    }
+  }
+  int rs = 0;
+  if (orp || bs_valid) {
+    const int bb = orp ? (bs_valid ? max(b, bs) : b) : bs;
+    rs = max(-200, min(200, bb - TC_UNITS_BITS));
+  }
+  const int F_new = F_old - rs;
+  const int shq = max(0, b - TC_QBITS);
+  const int R = (int)persist[4] + rs - shq - 64;
+  TcStepParams p;
+  p.step = n;
+  p.trace_row = trace_on ? persist[2] : -1;
+  for (int c = 0; c < 3; ++c) p.dU_src[c] = have_src ? llrint(ldexp(src[c], F_new)) : 0;
+  p.rs = rs;
+  p.shq = shq;
+  p.R = R;
+  p.F = F_new;
+  p.or_slot = (int)(n % 3);
+  p.rs_prev = (int)persist[5];
+  if (F_new < -2000 || F_new > 2000) atomicOr(status, 2);
+  *params = p;
+  or_slots[(n + 1) % 3] = 0;
+  persist[0] = F_new;
+  persist[5] = rs;
+  persist[1] = n + 1;
+  if (trace_on) persist[2] += 1;
+}
+
+int tc_smem_bytes() { return kSmemBytes; }
+
+cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t *persist,
+                                  const double *series, unsigned long long *or_slots,
+                                  double src_scale, const double dir[3], int have_src,
+                                  int trace_on, int *status) {
+  tc_prologue_kernel<<<1, 32, 0, s>>>(params, persist, series, or_slots, src_scale, dir[0],
+                                      dir[1], dir[2], have_src, trace_on, status);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_prepare() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(tc_step_kernel<TC_MODE_STEP>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(tc_step_kernel<TC_MODE_KU>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
+      cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(tc_step_kernel<TC_MODE_PARTIALS>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+template <int MODE>
+static cudaError_t launch_mode(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap) {
+  const int items = d.tiles_x * d.tiles_y * d.tiles_z;
+  tc_step_kernel<MODE><<<items, TC_THREADS, kSmemBytes, s>>>(*tmap, d);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode) {
+  switch (mode) {
+    case TC_MODE_STEP: return launch_mode<TC_MODE_STEP>(s, d, tmap);
+    case TC_MODE_KU: return launch_mode<TC_MODE_KU>(s, d, tmap);
+    default: return launch_mode<TC_MODE_PARTIALS>(s, d, tmap);
+  }
+}

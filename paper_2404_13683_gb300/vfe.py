@@ -1,0 +1,270 @@
+"""Thin Python binding of the C ABI in ``include/vfe.h``.
+
+Functions keep the C names and only marshal arguments (numpy arrays in,
+numpy arrays out).  Every step of the solver runs in the CUDA library
+``libvfe.so``; if that library cannot be loaded this module raises instead of
+falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VFE_OK = 0
+VFE_EINVAL = -1
+VFE_ENOMEM = -2
+VFE_ECUDA = -3
+VFE_ETIMEOUT = -4
+VFE_ESTATE = -5
+
+VFE_OVFEM = 0
+VFE_VFEM = 1
+VFE_PATH_FP64 = 0
+VFE_PATH_TC = 1
+
+# every entry point declared in include/vfe.h
+EXPORTS = (
+    "vfe_default_options", "vfe_create_mesh", "vfe_destroy", "vfe_set_source",
+    "vfe_set_receivers", "vfe_internal_force", "vfe_step", "vfe_synchronize",
+    "vfe_get_traces", "vfe_get_dt", "vfe_get_sizes", "vfe_get_step_count",
+    "vfe_get_state", "vfe_set_state", "vfe_last_error", "vfe_debug_tc_partials",
+)
+
+
+class VfeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("vfe error %d: %s" % (code, msg))
+        self.code = code
+
+
+class vfe_options(ctypes.Structure):
+    _fields_ = [("element_kind", ctypes.c_int), ("path", ctypes.c_int), ("stages", ctypes.c_int),
+                ("fix_bottom", ctypes.c_int), ("dt", ctypes.c_double),
+                ("cfl_fraction", ctypes.c_double), ("device", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load ``libvfe.so`` (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libvfe.so is missing; run paper_2404_13683_gb300.build.build()")
+    L = ctypes.CDLL(_build.LIB)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    L.vfe_default_options.argtypes = [ctypes.POINTER(vfe_options)]
+    L.vfe_default_options.restype = None
+    L.vfe_create_mesh.argtypes = [I, I, I, D, P, P, I, ctypes.POINTER(vfe_options),
+                                  ctypes.POINTER(ctypes.c_void_p)]
+    L.vfe_destroy.argtypes = [P]
+    L.vfe_set_source.argtypes = [P, I, I, I, P, D, D, D]
+    L.vfe_set_receivers.argtypes = [P, I, P]
+    L.vfe_internal_force.argtypes = [P, P, P]
+    L.vfe_step.argtypes = [P, I]
+    L.vfe_synchronize.argtypes = [P]
+    L.vfe_get_traces.argtypes = [P, P, ctypes.POINTER(I64)]
+    L.vfe_get_dt.argtypes = [P, ctypes.POINTER(D)]
+    L.vfe_get_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    L.vfe_get_step_count.argtypes = [P, ctypes.POINTER(I64)]
+    L.vfe_get_state.argtypes = [P, P, P]
+    L.vfe_set_state.argtypes = [P, P, P]
+    L.vfe_last_error.argtypes = []
+    L.vfe_last_error.restype = ctypes.c_char_p
+    L.vfe_debug_tc_partials.argtypes = [P, P, I, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    for name in EXPORTS:
+        if name not in ("vfe_default_options", "vfe_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != VFE_OK:
+        raise VfeError(rc, load().vfe_last_error().decode(errors="replace"))
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def vfe_last_error() -> str:
+    return load().vfe_last_error().decode(errors="replace")
+
+
+def vfe_default_options(**kw) -> vfe_options:
+    o = vfe_options()
+    load().vfe_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def vfe_create_mesh(nx, ny, nz, h, material_ids, material_table, opt=None):
+    ids = np.ascontiguousarray(material_ids, dtype=np.int32).reshape(-1)
+    tab = np.ascontiguousarray(material_table, dtype=np.float64).reshape(-1, 3)
+    if ids.size != nx * ny * nz:
+        raise ValueError("material_ids must have nx*ny*nz entries")
+    out = ctypes.c_void_p()
+    _check(load().vfe_create_mesh(int(nx), int(ny), int(nz), float(h), _p(ids), _p(tab),
+                                  len(tab), ctypes.byref(opt) if opt is not None else None,
+                                  ctypes.byref(out)))
+    return out
+
+
+def vfe_destroy(mesh):
+    _check(load().vfe_destroy(mesh))
+
+
+def vfe_set_source(mesh, i, j, k, direction, f0_hz, t0_s, amp):
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    _check(load().vfe_set_source(mesh, int(i), int(j), int(k), _p(d), float(f0_hz), float(t0_s),
+                                 float(amp)))
+
+
+def vfe_set_receivers(mesh, ijk):
+    a = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    _check(load().vfe_set_receivers(mesh, len(a), _p(a) if len(a) else None))
+
+
+def vfe_get_sizes(mesh):
+    nn, ne = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().vfe_get_sizes(mesh, ctypes.byref(nn), ctypes.byref(ne)))
+    return nn.value, ne.value
+
+
+def vfe_internal_force(mesh, u):
+    nn, _ = vfe_get_sizes(mesh)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    if u.size != 3 * nn:
+        raise ValueError("u must have 3*n_nodes entries")
+    f = np.empty_like(u)
+    _check(load().vfe_internal_force(mesh, _p(u), _p(f)))
+    return f
+
+
+def vfe_step(mesh, n):
+    _check(load().vfe_step(mesh, int(n)))
+
+
+def vfe_synchronize(mesh):
+    _check(load().vfe_synchronize(mesh))
+
+
+def vfe_get_traces(mesh, n_rec=None):
+    rows = ctypes.c_int64()
+    _check(load().vfe_get_traces(mesh, None, ctypes.byref(rows)))
+    if n_rec is None:
+        raise ValueError("n_rec is required")
+    out = np.zeros((rows.value, n_rec, 3))
+    if rows.value and n_rec:
+        _check(load().vfe_get_traces(mesh, _p(out), ctypes.byref(rows)))
+    return out
+
+
+def vfe_get_dt(mesh):
+    v = ctypes.c_double()
+    _check(load().vfe_get_dt(mesh, ctypes.byref(v)))
+    return v.value
+
+
+def vfe_get_step_count(mesh):
+    v = ctypes.c_int64()
+    _check(load().vfe_get_step_count(mesh, ctypes.byref(v)))
+    return v.value
+
+
+def vfe_get_state(mesh):
+    nn, _ = vfe_get_sizes(mesh)
+    u = np.zeros(3 * nn)
+    up = np.zeros(3 * nn)
+    _check(load().vfe_get_state(mesh, _p(u), _p(up)))
+    return u, up
+
+
+def vfe_set_state(mesh, u, u_prev):
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    up = np.ascontiguousarray(u_prev, dtype=np.float64).reshape(-1)
+    _check(load().vfe_set_state(mesh, _p(u), _p(up)))
+
+
+def vfe_debug_tc_partials(mesh, u, element_ids):
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    ids = np.ascontiguousarray(element_ids, dtype=np.int64).reshape(-1)
+    out = np.zeros((len(ids), 48), dtype=np.int64)
+    sh, fb = ctypes.c_int(), ctypes.c_int()
+    _check(load().vfe_debug_tc_partials(mesh, _p(u), len(ids), _p(ids), _p(out),
+                                        ctypes.byref(sh), ctypes.byref(fb)))
+    return out, sh.value, fb.value
+
+
+class Mesh:
+    """Owning wrapper over a ``vfe_mesh*`` built from a workload dictionary
+    (see ``workloads.py``)."""
+
+    def __init__(self, workload, path=VFE_PATH_TC, kind=VFE_OVFEM, stages=5, dt=0.0,
+                 fix_bottom=True, stream=None, device=0, source=True, receivers=True):
+        nx, ny, nz = workload["shape"]
+        opt = vfe_default_options(element_kind=kind, path=path, stages=stages, dt=dt,
+                                  fix_bottom=int(fix_bottom), device=device,
+                                  stream=stream or 0)
+        self.handle = vfe_create_mesh(nx, ny, nz, workload["h"], workload["material_ids"],
+                                      workload["material_table"], opt)
+        self.workload = workload
+        self.n_rec = 0
+        if source and workload.get("source") is not None:
+            s = workload["source"]
+            vfe_set_source(self.handle, *s["ijk"], s["dir"], s["f0"], s["t0"], s["amp"])
+        if receivers and workload.get("receivers") is not None:
+            self.set_receivers(workload["receivers"])
+
+    def set_receivers(self, ijk):
+        ijk = np.asarray(ijk, dtype=np.int32).reshape(-1, 3)
+        vfe_set_receivers(self.handle, ijk)
+        self.n_rec = len(ijk)
+
+    def step(self, n):
+        vfe_step(self.handle, n)
+
+    def synchronize(self):
+        vfe_synchronize(self.handle)
+
+    def traces(self):
+        return vfe_get_traces(self.handle, self.n_rec)
+
+    def internal_force(self, u):
+        return vfe_internal_force(self.handle, u)
+
+    @property
+    def dt(self):
+        return vfe_get_dt(self.handle)
+
+    def close(self):
+        if self.handle:
+            vfe_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
