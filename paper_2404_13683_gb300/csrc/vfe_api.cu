@@ -173,7 +173,11 @@ struct vfe_mesh {
   TcStepParams *d_tcparams = nullptr;
   int64_t *d_tcpersist = nullptr;
   CUtensorMap tmap[2];
-  int tiles_x = 0, tiles_y = 0, tiles_z = 0, cz = 0;
+  int tiles_x = 0, tiles_y = 0, n_ctas = 0;
+  std::vector<int4> segs;         // (tile x, tile y, z0, z1)
+  std::vector<int32_t> seg_off;   // CTA -> first segment
+  int4 *d_segs = nullptr;
+  int32_t *d_seg_off = nullptr;
   int e_ref = 0, eC = 0;
   double src_scale = 0.0;  // dt^2 / m at the source node
 
@@ -204,7 +208,8 @@ static TcDevice tc_device(const vfe_mesh *m, int cur) {
   TcDevice d;
   memset(&d, 0, sizeof(d));
   d.nx = m->nx; d.ny = m->ny; d.nz = m->nz; d.nxp = m->nxp;
-  d.tiles_x = m->tiles_x; d.tiles_y = m->tiles_y; d.tiles_z = m->tiles_z; d.cz = m->cz;
+  d.n_ctas = m->n_ctas;
+  d.segs = m->d_segs; d.seg_off = m->d_seg_off;
   d.n_mat = m->n_mat; d.stages = m->opt.stages; d.n_rec = m->n_rec;
   d.plane = m->plane; d.comp = m->comp;
   d.mat = m->d_mat; d.C = m->d_C;
@@ -300,7 +305,8 @@ int vfe_destroy(vfe_mesh *m) {
   void *ptrs[] = {m->d_mat, m->d_status, m->d_series, m->d_traces, m->d_u[0], m->d_u[1],
                   m->d_dt2m, m->d_K, m->d_recnodes, m->d_f64params, m->d_f64persist,
                   m->d_U[0], m->d_U[1], m->d_C, m->d_Bop, m->d_mats, m->d_recv,
-                  m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist};
+                  m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist, m->d_segs,
+                  m->d_seg_off};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -511,20 +517,19 @@ static int build_tc(vfe_mesh *m) {
           }
           bop[((kg * 6 + ng) * 8 + r) * 8 + l] = __half_as_ushort(__float2half(v));
         }
-  // per-material multipliers with a common unit 2^(64 - e_ref)
+  // per-material multipliers in one mesh-wide unit: A = kappa ds/256 2^e_ref,
+  // B = G ds/384 2^e_ref, the largest in [2^60, 2^61).  With |q| < 2^51 an
+  // element term (|P| A + |Q| B)/2^63 stays below 1258 2^49 and a node sum
+  // of eight below 2^63.
   std::vector<TcMaterial> mats(m->n_mat);
-  std::vector<int> em(m->n_mat);
-  int e_ref = 1 << 30;
+  double mxall = 0.0;
+  for (int i = 0; i < m->n_mat; ++i)
+    mxall = std::max(mxall, std::max(m->kappa[i] * m->h / 256.0, m->G[i] * m->h / 384.0));
+  const int e_ref = 60 - std::ilogb(mxall);
   for (int i = 0; i < m->n_mat; ++i) {
-    const double kd = m->kappa[i] * m->h / 256.0, gd = m->G[i] * m->h / 384.0;
-    const double mx = std::max(kd, gd);
-    em[i] = 59 - std::ilogb(mx);
-    e_ref = std::min(e_ref, em[i]);
-  }
-  for (int i = 0; i < m->n_mat; ++i) {
-    mats[i].A = llrint(std::ldexp(m->kappa[i] * m->h / 256.0, em[i]));
-    mats[i].B = llrint(std::ldexp(m->G[i] * m->h / 384.0, em[i]));
-    mats[i].shift = std::min(em[i] - e_ref, 63);
+    mats[i].A = llrint(std::ldexp(m->kappa[i] * m->h / 256.0, e_ref));
+    mats[i].B = llrint(std::ldexp(m->G[i] * m->h / 384.0, e_ref));
+    mats[i].shift = 0;
     mats[i].pad = 0;
   }
   m->e_ref = e_ref;
@@ -541,18 +546,32 @@ static int build_tc(vfe_mesh *m) {
   std::vector<int64_t> C(m->plane * (nz + 1), 0);
   for (int64_t n = 0; n < m->nn; ++n)
     if (!m->fixed[n]) C[tc_index(m, n)] = llrint(std::ldexp(m->dt * m->dt / m->mass[n], m->eC));
-  // work decomposition: choose the z chunk that minimises waves x layers
+  // work decomposition: the column-planes (15x15 node column, one node
+  // plane) in column order are split into one equal contiguous range per SM;
+  // each range becomes one or more segments (column, z0, z1)
   m->tiles_x = (nx + 1 + TC_OWN - 1) / TC_OWN;
   m->tiles_y = (ny + 1 + TC_OWN - 1) / TC_OWN;
-  const int planes = nz + 1;
-  double best = 1e300;
-  for (int cz = 1; cz <= planes; ++cz) {
-    const int64_t items = (int64_t)m->tiles_x * m->tiles_y * ((planes + cz - 1) / cz);
-    const double waves = std::ceil((double)items / m->sms);
-    const double cost = waves * (cz + 1) + 0.02 * cz;
-    if (cost < best) { best = cost; m->cz = cz; }
+  {
+    const int64_t planes = nz + 1, ncols = (int64_t)m->tiles_x * m->tiles_y;
+    const int64_t total = ncols * planes;
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(m->sms, total));
+    m->n_ctas = (int)G;
+    m->segs.clear();
+    m->seg_off.assign(G + 1, 0);
+    for (int64_t b = 0; b < G; ++b) {
+      m->seg_off[b] = (int32_t)m->segs.size();
+      int64_t lo = b * total / G;
+      const int64_t hi = (b + 1) * total / G;
+      while (lo < hi) {
+        const int64_t col = lo / planes, z0 = lo % planes;
+        const int64_t z1 = std::min<int64_t>(planes, z0 + (hi - lo));
+        m->segs.push_back(make_int4((int)(col % m->tiles_x), (int)(col / m->tiles_x), (int)z0,
+                                    (int)z1));
+        lo += z1 - z0;
+      }
+    }
+    m->seg_off[G] = (int32_t)m->segs.size();
   }
-  m->tiles_z = (planes + m->cz - 1) / m->cz;
 
   const size_t ubytes = sizeof(int64_t) * 3 * m->comp;
   CUDA_TRY(cudaMalloc(&m->d_U[0], ubytes));
@@ -563,6 +582,12 @@ static int build_tc(vfe_mesh *m) {
   CUDA_TRY(cudaMalloc(&m->d_or, sizeof(unsigned long long) * 3));
   CUDA_TRY(cudaMalloc(&m->d_tcparams, sizeof(TcStepParams)));
   CUDA_TRY(cudaMalloc(&m->d_tcpersist, sizeof(int64_t) * 8));
+  CUDA_TRY(cudaMalloc(&m->d_segs, sizeof(int4) * m->segs.size()));
+  CUDA_TRY(cudaMalloc(&m->d_seg_off, sizeof(int32_t) * m->seg_off.size()));
+  CUDA_TRY(cudaMemcpy(m->d_segs, m->segs.data(), sizeof(int4) * m->segs.size(),
+                      cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->d_seg_off, m->seg_off.data(), sizeof(int32_t) * m->seg_off.size(),
+                      cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(m->d_U[0], 0, ubytes));
   CUDA_TRY(cudaMemset(m->d_U[1], 0, ubytes));
   CUDA_TRY(cudaMemcpy(m->d_C, C.data(), sizeof(int64_t) * C.size(), cudaMemcpyHostToDevice));
@@ -596,24 +621,30 @@ static int rebuild_receivers(vfe_mesh *m) {
   if (m->opt.path == VFE_PATH_TC) {
     int64_t persist2 = 0;
     CUDA_TRY(cudaMemcpy(m->d_tcpersist + 2, &persist2, sizeof(int64_t), cudaMemcpyHostToDevice));
-    const int items = m->tiles_x * m->tiles_y * m->tiles_z;
+    const int items = (int)m->segs.size();
     std::vector<std::vector<TcRecv>> per(items);
     for (int r = 0; r < m->n_rec; ++r) {
       const int i = m->rec_ijk[3 * r], j = m->rec_ijk[3 * r + 1], k = m->rec_ijk[3 * r + 2];
-      const int tx = i / TC_OWN, ty = j / TC_OWN, tz = k / m->cz;
+      const int tx = i / TC_OWN, ty = j / TC_OWN;
       TcRecv v;
       v.ei = (int16_t)(i - TC_OWN * tx);
       v.ej = (int16_t)(j - TC_OWN * ty);
       v.k = k;
       v.r = r;
       v.pad = 0;
-      per[tx + m->tiles_x * (ty + m->tiles_y * tz)].push_back(v);
+      for (int sg = 0; sg < items; ++sg) {
+        const int4 q = m->segs[sg];
+        if (q.x == tx && q.y == ty && k >= q.z && k < q.w) {
+          per[sg].push_back(v);
+          break;
+        }
+      }
     }
     std::vector<TcRecv> flat;
     std::vector<int32_t> off(items + 1, 0);
     for (int it = 0; it < items; ++it) {
       if ((int)per[it].size() > TC_MAX_REC_CTA)
-        return fail(VFE_EINVAL, "more than %d receivers in one %dx%d node column chunk",
+        return fail(VFE_EINVAL, "more than %d receivers in one %dx%d node column segment",
                     TC_MAX_REC_CTA, TC_OWN, TC_OWN);
       off[it] = (int32_t)flat.size();
       flat.insert(flat.end(), per[it].begin(), per[it].end());
@@ -971,7 +1002,7 @@ int vfe_internal_force(vfe_mesh *m, const double *u, double *f) {
     int shq = 0, F = 0;
     int rc = tc_apply(m, u, TC_MODE_KU, S, &shq, &F);
     if (rc != VFE_OK) return rc;
-    const int ex = 64 - m->e_ref + shq - F;
+    const int ex = 63 - m->e_ref + shq - F;
     for (int64_t n = 0; n < m->nn; ++n) {
       const int64_t t = tc_index(m, n);
       for (int c = 0; c < 3; ++c) f[3 * n + c] = std::ldexp((double)S[c * m->comp + t], ex);

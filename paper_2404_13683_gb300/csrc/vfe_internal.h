@@ -19,12 +19,12 @@
 #define TC_BOXX 18               // TMA box width in x (int64; 144 B)
 #define TC_MAX_STAGES 5          // 11-bit digit stages (5 x 11 = 55 bits)
 #define TC_DIGIT_BITS 11
-#define TC_QBITS 52              // |q| < 2^52 after the per-step shift
+#define TC_QBITS 51              // |q| < 2^51 after the per-step shift
 #define TC_N 48                  // MMA N: 24 K^kappa rows + 24 K^G' rows
-#define TC_THREADS 256
+#define TC_THREADS 512          // two threads per element: corner groups dz = 0 / 1
 #define TC_MAX_MAT 64            // materials per mesh on the TC path
 #define TC_MAX_REC_CTA 64        // receivers handled per CTA work item
-#define TC_UNITS_BITS 58         // target bit length of max |U| after rescale
+#define TC_UNITS_BITS 56         // target bit length of max |U| after rescale
 
 // fp32 magic bias: 8 padding K-rows carry A = 128, B = 12288 so that every
 // accumulator starts from 1.5 * 2^23; its bit pattern is then 0x4B400000 + d
@@ -46,10 +46,10 @@ struct TcStepParams {     // written by the per-step prologue kernel
                           // units 2^-(F_old + rs_prev)
 };
 
-struct TcMaterial {       // per-material integer multipliers
-  int64_t A;              // round(kappa ds/256 * 2^e), <= 2^60
-  int64_t B;              // round(G ds/384 * 2^e)
-  int shift;              // e - e_ref (>= 0): right shift to the common unit
+struct TcMaterial {       // per-material integer multipliers, mesh-wide unit
+  int64_t A;              // round(kappa ds/256 * 2^e_ref) < 2^61
+  int64_t B;              // round(G ds/384 * 2^e_ref)
+  int shift;              // unused (0)
   int pad;
 };
 
@@ -62,7 +62,7 @@ struct TcRecv {           // receiver handled by a CTA work item
 
 struct TcDevice {         // everything the TC kernels read (by value)
   int nx, ny, nz, nxp;    // nxp: padded x pitch of nodal arrays (multiple of 4)
-  int tiles_x, tiles_y, tiles_z, cz;  // work decomposition; cz planes per chunk
+  int n_ctas;             // one CTA per SM; CTA b owns segments seg_off[b..b+1)
   int n_mat, stages, n_rec;
   int64_t plane;          // nxp*(ny+1): nodal plane stride
   int64_t comp;           // plane*(nz+1): component stride
@@ -72,8 +72,10 @@ struct TcDevice {         // everything the TC kernels read (by value)
   int64_t *U_next;        // same buffer as U_prev
   const uint16_t *Bop;    // B operand image (fp16 bits), 48x32, core-matrix order
   const TcMaterial *mats;
-  const TcRecv *recv;     // receivers, grouped per work item
-  const int32_t *recv_off;// work item -> first receiver, size items+1
+  const int4 *segs;       // (tile x, tile y, first owned plane, end plane)
+  const int32_t *seg_off; // CTA -> first segment, size n_ctas+1
+  const TcRecv *recv;     // receivers, grouped per segment
+  const int32_t *recv_off;// segment -> first receiver, size n_segs+1
   int64_t src_node;       // -1: none
   double *traces;         // [rows][n_rec][3]
   unsigned long long *or_slots;  // 3 slots of OR(|U_new|)

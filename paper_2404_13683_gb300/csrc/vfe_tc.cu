@@ -14,7 +14,7 @@
 //     K_e u_e = ds (kappa/256 P + G/384 Q) (Eq. GE:TC with the kappa and G
 //     parts kept separate, so the digits are per node, not per element).
 //   * Scaling (Eq. intscaling): one power-of-two shift per step puts every
-//     node value below 2^52 (q = floor(U / 2^shq)).
+//     node value below 2^51 (q = floor(U / 2^shq)).
 //   * Hierarchical split (Eq. int8comp1): q = sum_s 2^(11 s) d_s with balanced
 //     digits d_s in [-1024, 1023] (offset-binary extraction), fp16-exact.
 //   * Recombination (Eq. int8comp2): sum_s 2^(11 s) D_s in int64.
@@ -50,12 +50,14 @@ constexpr int kUSlotStride = (kUSlotBytes + 127) / 128 * 128;  // TMA smem dst: 
 constexpr int kUSlots = 4;
 constexpr int kBopBytes = TC_N * 32 * 2;
 constexpr int kYbufBytes = 2 * TC_EX * TC_EX * 3 * 8;
+constexpr int kCbufBytes = 2 * TC_EX * TC_EX * 3 * 8;     // z carry, double buffered
 
 constexpr int kOffDigits = 0;
 constexpr int kOffU = kOffDigits + kDigitSlots * kDigitSlotBytes;
 constexpr int kOffBop = kOffU + kUSlots * kUSlotStride;
 constexpr int kOffYbuf = kOffBop + kBopBytes;
-constexpr int kOffMat = kOffYbuf + kYbufBytes;
+constexpr int kOffCbuf = kOffYbuf + kYbufBytes;
+constexpr int kOffMat = kOffCbuf + kCbufBytes;
 constexpr int kOffRecv = kOffMat + TC_MAX_MAT * (int)sizeof(TcMaterial);
 constexpr int kOffBar = kOffRecv + TC_MAX_REC_CTA * (int)sizeof(TcRecv);
 constexpr int kOffMisc = kOffBar + 8 * 8;
@@ -197,10 +199,75 @@ __device__ __forceinline__ int acc_to_int(uint32_t w) { return (int)w - TC_MAGIC
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Epilogue arithmetic.
+// ---------------------------------------------------------------------------
+// Exact P = sum_s 2^(11 s) D_s from the five magic-biased accumulator words
+// w_s = 0x4B400000 + D_s of one output, as one mad.wide chain: the biased
+// words are combined unsigned and the bias removed once (mod 2^64 arithmetic
+// is exact because the true P fits in int64).  |q| < 2^51 keeps |D_4| < 2^18,
+// so (w_4 - bias) * 4096 fits the high word.
+__device__ __forceinline__ int64_t recombine5(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                              uint32_t w4) {
+  constexpr uint64_t kBias = (uint64_t)TC_MAGIC_BITS * (1ull + 2048ull + 4194304ull + 8589934592ull);
+  uint64_t p;
+  asm("{\n"
+      " .reg .u64 t;\n"
+      " .reg .u32 lo, hi, d4;\n"
+      " mov.b64 t, {%1, 0};\n"
+      " mad.wide.u32 t, %2, 2048, t;\n"
+      " mad.wide.u32 t, %3, 4194304, t;\n"
+      " mov.b64 {lo, hi}, t;\n"
+      " mad.lo.u32 hi, %4, 2, hi;\n"
+      " sub.u32 d4, %5, %6;\n"
+      " mad.lo.u32 hi, d4, 4096, hi;\n"
+      " sub.cc.u32 lo, lo, %7;\n"
+      " subc.u32 hi, hi, %8;\n"
+      " mov.b64 %0, {lo, hi};\n"
+      "}\n"
+      : "=l"(p)
+      : "r"(w0), "r"(w1), "r"(w2), "r"(w3), "r"(w4), "r"((uint32_t)TC_MAGIC_BITS),
+        "r"((uint32_t)kBias), "r"((uint32_t)(kBias >> 32)));
+  return (int64_t)p;
+}
+
+// floor((P A + Q B) / 2^63) within 4 units, for the material multipliers
+// A = A1 2^31 + A0, B = B1 2^31 + B0 (0 <= A0, B0 < 2^31; 0 <= A1, B1 < 2^30)
+// and |P|, |Q| < 2^61:  P A / 2^63 = P1 A1 + (P1 A0 + P0 A1 / 2) / 2^31 + ...
+// with P = P1 2^32 + P0; the P0 A0 term is dropped.
+__device__ __forceinline__ int64_t mul2_hi63(int64_t P, int64_t Q, int A1, int A0, int B1,
+                                             int B0) {
+  int64_t r;
+  asm("{\n"
+      " .reg .u32 p0, p1, q0, q1;\n"
+      " .reg .u64 lo, res;\n"
+      " .reg .s64 mid;\n"
+      " mov.b64 {p0, p1}, %1;\n"
+      " mov.b64 {q0, q1}, %2;\n"
+      " mul.wide.u32 lo, p0, %3;\n"
+      " mad.wide.u32 lo, q0, %5, lo;\n"
+      " shr.u64 lo, lo, 1;\n"
+      " mul.wide.s32 mid, p1, %4;\n"
+      " mad.wide.s32 mid, q1, %6, mid;\n"
+      " add.s64 mid, mid, lo;\n"
+      " shr.s64 mid, mid, 31;\n"
+      " mul.wide.s32 res, p1, %3;\n"
+      " mad.wide.s32 res, q1, %5, res;\n"
+      " add.s64 %0, res, mid;\n"
+      "}\n"
+      : "=l"(r)
+      : "l"(P), "l"(Q), "r"(A1), "r"(A0), "r"(B1), "r"(B0));
+  return r;
+}
+
+// ---------------------------------------------------------------------------
 // The fused kernel.  MODE: 0 = time step, 1 = K u only (writes S), 2 = exact
 // partial products per element (diagnostic).
+//
+// Work: CTA b walks the segments seg_off[b] .. seg_off[b+1]-1; a segment is a
+// 15x15 node column (tx, ty) and a range of owned node planes [z0, z1).  The
+// host balances column-planes across CTAs, so every SM gets the same work.
 // ---------------------------------------------------------------------------
-template <int MODE>
+template <int MODE, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_step_kernel(const __grid_constant__ CUtensorMap tmap_u, const TcDevice d) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -208,41 +275,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   int64_t *uslot = reinterpret_cast<int64_t *>(smem + kOffU);
   uint16_t *bop = reinterpret_cast<uint16_t *>(smem + kOffBop);
   int64_t *ybuf = reinterpret_cast<int64_t *>(smem + kOffYbuf);
+  int64_t *cbuf = reinterpret_cast<int64_t *>(smem + kOffCbuf);
   TcMaterial *smat = reinterpret_cast<TcMaterial *>(smem + kOffMat);
   TcRecv *srecv = reinterpret_cast<TcRecv *>(smem + kOffRecv);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..3: U slots, 4: MMA
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..3: U slots, 4,5: MMA tiles
   uint32_t *misc = reinterpret_cast<uint32_t *>(smem + kOffMisc);  // [0] tmem base, [1] abort
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int item = blockIdx.x;
-  const int tx = item % d.tiles_x;
-  const int ty = (item / d.tiles_x) % d.tiles_y;
-  const int tz = item / (d.tiles_x * d.tiles_y);
-  const int X0 = TC_OWN * tx - 1;  // global x of local element/node column 0
-  const int Y0 = TC_OWN * ty - 1;
-  const int Z0 = tz * d.cz;
-  const int Z1 = min(Z0 + d.cz, d.nz + 1);  // owned node planes [Z0, Z1)
-  const int xbox = X0 & ~1;                 // TMA x must be even (16-byte rule)
-  const int xo = X0 - xbox;                 // 0 or 1: local node ni sits at box x = ni + xo
-
   const TcStepParams P = *d.params;
   // with fewer stages the low digits are dropped (the top ones carry the value)
-  const int s_lo = TC_MAX_STAGES - d.stages;
+  constexpr int s_lo = TC_MAX_STAGES - STAGES;
 
-  // thread <-> element: TMEM lane m of tile t holds element (m % 16, 8 t + m / 16)
-  const int tile = warp >> 2;
+  // thread <-> element: TMEM lane m of tile t holds element (m % 16, 8 t + m / 16);
+  // warps 0-7 take the corner groups with dz = 0, warps 8-15 those with dz = 1
+  const int half = warp >> 3;
+  const int tile = (warp >> 2) & 1;
   const int m_row = ((warp & 3) << 5) + lane;
   const int ei = m_row & 15;
   const int ej = 8 * tile + (m_row >> 4);
-  const int gi = X0 + ei + 1, gj = Y0 + ej + 1;  // this thread's node (ei+1, ej+1)
-  const bool own_xy = (ei < TC_OWN) && (ej < TC_OWN) && gi <= d.nx && gj <= d.ny;
 
   // ---- one-time setup ------------------------------------------------------
   if (tid == 0) {
     misc[1] = 0;
     for (int i = 0; i < kUSlots; ++i) mbar_init(&bars[i], 1);
     mbar_init(&bars[4], 1);
+    mbar_init(&bars[5], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -251,24 +309,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // B operand image and material table
   for (int i = tid; i < kBopBytes / 16; i += TC_THREADS)
     reinterpret_cast<uint4 *>(bop)[i] = reinterpret_cast<const uint4 *>(d.Bop)[i];
   for (int i = tid; i < d.n_mat; i += TC_THREADS) smat[i] = d.mats[i];
-  // receivers of this work item
-  int rbeg = 0, nrec = 0;
-  if (MODE == TC_MODE_STEP && d.n_rec > 0 && P.trace_row >= 0) {
-    rbeg = d.recv_off[item];
-    nrec = min(d.recv_off[item + 1] - rbeg, TC_MAX_REC_CTA);
-    for (int i = tid; i < nrec; i += TC_THREADS) srecv[i] = d.recv[rbeg + i];
-  }
-  // magic rows (lines 6 and 7 of every block) of every digit slot and stage
-  {
+  {  // magic rows (lines 6 and 7 of every block) of every digit slot and stage
     const uint32_t mg = (uint32_t)__half_as_ushort(__float2half(TC_MAGIC_A));
     const uint4 mv = make_uint4(mg | (mg << 16), mg | (mg << 16), mg | (mg << 16), mg | (mg << 16));
     const int nblocks = kDigitSlots * TC_MAX_STAGES * TC_NODES * 2;
     for (int i = tid; i < 2 * nblocks; i += TC_THREADS) {
-      int blk = i >> 1, line = 6 + (i & 1);
+      const int blk = i >> 1, line = 6 + (i & 1);
       *reinterpret_cast<uint4 *>(digits + blk * kBlockBytes + line * 16) = mv;
     }
   }
@@ -277,272 +326,299 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = misc[0];
 
-  uint32_t uphase = 0;    // parity bit per U slot
+  uint32_t uphase = 0;   // parity bit per U slot
   uint32_t mma_phase = 0;
   bool aborted = false;
+  unsigned long long or_acc = 0;
+  const TcMaterial zero_mat = {0, 0, 0, 0};
 
-  auto issue_plane = [&](int p) {  // TMA of node plane p into U slot p & 3
-    if (tid == 0) {
-      int s = p & 3;
-      mbar_expect_tx(&bars[s], kUSlotBytes);
-      tma_load_u(uslot + s * (kUSlotStride / 8), &tmap_u, &bars[s], xbox, Y0, p);
-    }
-  };
-  // all threads wait for plane p; returns false on timeout
-  auto wait_plane = [&](int p) -> bool {
-    int s = p & 3;
-    bool ok = mbar_wait(&bars[s], (uphase >> s) & 1u);
-    uphase ^= 1u << s;
-    return ok;
-  };
-  // digitise node plane p into digit slot p mod 3 (threads 0..101)
-  auto digitise = [&](int p) {
-    if (tid < TC_NODES * 6) {
-      const int nj = tid / 6, r = tid % 6, xc = r / 3, c = r % 3;
-      const int64_t *src = uslot + (p & 3) * (kUSlotStride / 8) + (c * TC_NODES + nj) * TC_BOXX +
-                           8 * xc + xo;
-      // offset-binary bias sum_s 1024 * 2^(11 s) over the 5 digit positions
-      const int64_t boff = (1LL << 10) | (1LL << 21) | (1LL << 32) | (1LL << 43) | (1LL << 54);
-      int64_t v[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) v[i] = shr_floor(src[i], P.shq) + boff;
-      unsigned char *slot = digits + ((p % kDigitSlots + kDigitSlots) % kDigitSlots) * kDigitSlotBytes;
-      for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
-        float f[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-          f[i] = int_to_f32_exact((int)((v[i] >> (TC_DIGIT_BITS * s)) & 2047) - 1024);
-        uint4 lo, hi;  // dx = 0 line: nodes 0..7, dx = 1 line: nodes 1..8
-        __half2 h;
-        h = __floats2half2_rn(f[0], f[1]); lo.x = *reinterpret_cast<uint32_t *>(&h);
-        h = __floats2half2_rn(f[2], f[3]); lo.y = *reinterpret_cast<uint32_t *>(&h);
-        h = __floats2half2_rn(f[4], f[5]); lo.z = *reinterpret_cast<uint32_t *>(&h);
-        h = __floats2half2_rn(f[6], f[7]); lo.w = *reinterpret_cast<uint32_t *>(&h);
-        h = __floats2half2_rn(f[1], f[2]); hi.x = *reinterpret_cast<uint32_t *>(&h);
-        h = __floats2half2_rn(f[3], f[4]); hi.y = *reinterpret_cast<uint32_t *>(&h);
-        h = __floats2half2_rn(f[5], f[6]); hi.z = *reinterpret_cast<uint32_t *>(&h);
-        h = __floats2half2_rn(f[7], f[8]); hi.w = *reinterpret_cast<uint32_t *>(&h);
-        unsigned char *blk = slot + s * kStageBytes + (nj * 2 + xc) * kBlockBytes;
-        *reinterpret_cast<uint4 *>(blk + c * 16) = lo;
-        *reinterpret_cast<uint4 *>(blk + (3 + c) * 16) = hi;
-      }
-    }
-  };
-  // one thread issues the MMAs of element layer L (node planes L, L+1)
-  auto issue_mma = [&](int L) {
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t bbase = smem_u32(bop);
-      for (int t = 0; t < 2; ++t)
-        for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
-          const uint32_t dcol = tmem_base + (uint32_t)(t * kTileCols + s * TC_N);
-          for (int dz = 0; dz < 2; ++dz) {
-            const int p = L + dz;
-            const int slot = ((p % kDigitSlots) + kDigitSlots) % kDigitSlots;
-            const uint32_t abase = smem_u32(digits + slot * kDigitSlotBytes + s * kStageBytes +
-                                            (16 * t) * kBlockBytes);
-            // A (MN-major): 8-element chunks at 128 B, K groups (dy) at 256 B
-            const uint64_t adesc = make_sdesc(abase, 2 * kBlockBytes, kBlockBytes);
-            // B (K-major): 8-row N groups at 128 B, K groups at 6*128 B
-            const uint64_t bdesc = make_sdesc(bbase + dz * 2 * 6 * kBlockBytes, 6 * kBlockBytes,
-                                              kBlockBytes);
-            mma_f16(dcol, adesc, bdesc, dz);
-          }
-        }
-      mma_commit(&bars[4]);
-    }
-  };
   auto sync_abort = [&](bool ok) -> bool {  // true if the CTA must stop
     if (!ok) atomicExch(&misc[1], 1u);
     __syncthreads();
     return misc[1] != 0;
   };
 
-  // ---- prologue: planes Z0-1, Z0, Z0+1 ------------------------------------
-  const int Lfirst = Z0 - 1, Llast = Z1 - 1;
-  issue_plane(Lfirst);
-  issue_plane(Lfirst + 1);
-  issue_plane(Lfirst + 2);
-  bool ok = wait_plane(Lfirst);
-  ok = wait_plane(Lfirst + 1) && ok;
-  aborted = sync_abort(ok);
-  if (!aborted) {
+  const int sbeg = d.seg_off[blockIdx.x], send = d.seg_off[blockIdx.x + 1];
+  for (int sg = sbeg; sg < send && !aborted; ++sg) {
+    const int4 seg = d.segs[sg];
+    const int X0 = TC_OWN * seg.x - 1;  // global x of local element/node column 0
+    const int Y0 = TC_OWN * seg.y - 1;
+    const int Z0 = seg.z, Z1 = seg.w;   // owned node planes [Z0, Z1)
+    const int xbox = X0 & ~1;           // TMA x must be even (16-byte rule)
+    const int xo = X0 - xbox;           // local node ni sits at box x = ni + xo
+    const int gi = X0 + ei + 1, gj = Y0 + ej + 1;  // this thread's node (ei+1, ej+1)
+    const bool own_xy = (ei < TC_OWN) && (ej < TC_OWN) && gi <= d.nx && gj <= d.ny;
+    const bool updater = own_xy && half == 0;  // half 0 owns the node update
+    const int gx = X0 + ei, gy = Y0 + ej;          // this thread's element column
+    const bool elem_xy = gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+
+    // receivers of this segment (the previous segment's reads are fenced by
+    // the barriers of its last layer)
+    int nrec = 0;
+    if (MODE == TC_MODE_STEP && d.n_rec > 0 && P.trace_row >= 0) {
+      const int rbeg = d.recv_off[sg];
+      nrec = min(d.recv_off[sg + 1] - rbeg, TC_MAX_REC_CTA);
+      for (int i = tid; i < nrec; i += TC_THREADS) srecv[i] = d.recv[rbeg + i];
+    }
+
+    auto issue_plane = [&](int p) {  // TMA of node plane p into U slot p & 3
+      if (tid == 0) {
+        const int s = p & 3;
+        mbar_expect_tx(&bars[s], kUSlotBytes);
+        tma_load_u(uslot + s * (kUSlotStride / 8), &tmap_u, &bars[s], xbox, Y0, p);
+      }
+    };
+    auto wait_plane = [&](int p) -> bool {
+      const int s = p & 3;
+      const bool ok = mbar_wait(&bars[s], (uphase >> s) & 1u);
+      uphase ^= 1u << s;
+      return ok;
+    };
+    // digitise node plane p into digit slot p mod 3: one task per (row,
+    // x-chunk, component, stage) writes the dx = 0 and dx = 1 lines.  With the
+    // offset-binary bias boff = sum_s 1024 2^(11 s), digit s of floor(U/2^shq)
+    // is ((U + boff 2^shq) >> (shq + 11 s)) & 2047 - 1024 (nested floors);
+    // U + boff 2^shq is positive and below 2^63 because |U| < 2^(51+shq) and
+    // shq <= 8 (|U| < 2^59).
+    constexpr int ntask = TC_NODES * 6 * STAGES;
+    const int dtask = tid < ntask ? tid : -1;
+    const int ds_ = s_lo + (dtask < 0 ? 0 : dtask / (TC_NODES * 6));
+    const int dr_ = dtask < 0 ? 0 : dtask % (TC_NODES * 6);
+    const int dnj = dr_ / 6, dxc = (dr_ % 6) / 3, dc = dr_ % 3;
+    const int dsrc = (dc * TC_NODES + dnj) * TC_BOXX + 8 * dxc + xo;
+    const int ddst = ds_ * kStageBytes + (dnj * 2 + dxc) * kBlockBytes + dc * 16;
+    const uint64_t dbias = (uint64_t)((1LL << 10) | (1LL << 21) | (1LL << 32) | (1LL << 43) |
+                                      (1LL << 54)) << P.shq;
+    const int dshift = P.shq + TC_DIGIT_BITS * ds_;
+    auto digitise = [&](int p) {
+      if (dtask < 0) return;
+      const int64_t *src = uslot + (p & 3) * (kUSlotStride / 8) + dsrc;
+      unsigned char *dst =
+          digits + ((p % kDigitSlots + kDigitSlots) % kDigitSlots) * kDigitSlotBytes + ddst;
+      float f[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const uint64_t v = (uint64_t)src[i] + dbias;
+        f[i] = int_to_f32_exact((int)((uint32_t)(v >> dshift) & 2047u) - 1024);
+      }
+      uint4 lo, hi;  // dx = 0 line: nodes 0..7, dx = 1 line: nodes 1..8
+      __half2 h;
+      h = __floats2half2_rn(f[0], f[1]); lo.x = *reinterpret_cast<uint32_t *>(&h);
+      h = __floats2half2_rn(f[2], f[3]); lo.y = *reinterpret_cast<uint32_t *>(&h);
+      h = __floats2half2_rn(f[4], f[5]); lo.z = *reinterpret_cast<uint32_t *>(&h);
+      h = __floats2half2_rn(f[6], f[7]); lo.w = *reinterpret_cast<uint32_t *>(&h);
+      h = __floats2half2_rn(f[1], f[2]); hi.x = *reinterpret_cast<uint32_t *>(&h);
+      h = __floats2half2_rn(f[3], f[4]); hi.y = *reinterpret_cast<uint32_t *>(&h);
+      h = __floats2half2_rn(f[5], f[6]); hi.z = *reinterpret_cast<uint32_t *>(&h);
+      h = __floats2half2_rn(f[7], f[8]); hi.w = *reinterpret_cast<uint32_t *>(&h);
+      *reinterpret_cast<uint4 *>(dst) = lo;
+      *reinterpret_cast<uint4 *>(dst + 48) = hi;
+    };
+    // one thread issues the MMAs of element layer L (node planes L, L+1),
+    // tile 0 first, with one commit per tile
+    auto issue_mma = [&](int L) {
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t bbase = smem_u32(bop);
+        for (int t = 0; t < 2; ++t) {
+          for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
+            const uint32_t dcol = tmem_base + (uint32_t)(t * kTileCols + s * TC_N);
+            for (int dz = 0; dz < 2; ++dz) {
+              const int p = L + dz;
+              const int slot = ((p % kDigitSlots) + kDigitSlots) % kDigitSlots;
+              const uint32_t abase = smem_u32(digits + slot * kDigitSlotBytes + s * kStageBytes +
+                                              (16 * t) * kBlockBytes);
+              // A (MN-major): 8-element chunks at 128 B, K groups (dy) at 256 B
+              const uint64_t adesc = make_sdesc(abase, 2 * kBlockBytes, kBlockBytes);
+              // B (K-major): 8-row N groups at 128 B, K groups at 6*128 B
+              const uint64_t bdesc = make_sdesc(bbase + dz * 2 * 6 * kBlockBytes, 6 * kBlockBytes,
+                                                kBlockBytes);
+              mma_f16(dcol, adesc, bdesc, dz);
+            }
+          }
+          mma_commit(&bars[4 + t]);
+        }
+      }
+    };
+
+    // ---- segment prologue: planes Z0-1, Z0, Z0+1 ---------------------------
+    const int Lfirst = Z0 - 1, Llast = Z1 - 1;
+    issue_plane(Lfirst);
+    issue_plane(Lfirst + 1);
+    issue_plane(Lfirst + 2);
+    bool ok = wait_plane(Lfirst);
+    ok = wait_plane(Lfirst + 1) && ok;
+    if (sync_abort(ok)) { aborted = true; break; }
     digitise(Lfirst);
     digitise(Lfirst + 1);
     fence_async_smem();
     __syncthreads();
     issue_mma(Lfirst);
-  }
 
-  // per-thread running state
-  int64_t carry[3] = {0, 0, 0};          // forces on (ei+1, ej+1) at plane L from layer L-1
-  unsigned long long or_acc = 0;
-  const TcMaterial zero_mat = {0, 0, 0, 0};
-
-  for (int L = Lfirst; L <= Llast && !aborted; ++L) {
-    // element material for this layer (void outside the mesh)
-    const int gx = X0 + ei, gy = Y0 + ej;
-    int m = -1;
-    if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && L >= 0 && L < d.nz)
-      m = d.mat[(int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L)];
-    // update operands of plane L (prefetched before the epilogue)
-    int64_t uprev[3] = {0, 0, 0}, cn = 0;
-    const bool upd = (MODE == TC_MODE_STEP) && own_xy && L >= Z0;
-    const int64_t nidx = (int64_t)L * d.plane + (int64_t)gj * d.nxp + gi;
-    if (upd) {
-      cn = d.C[nidx];
+    for (int L = Lfirst; L <= Llast; ++L) {
+      int m = -1;
+      if (elem_xy && L >= 0 && L < d.nz)
+        m = d.mat[(int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L)];
+      int64_t uprev[3] = {0, 0, 0}, cn = 0;
+      const bool upd = (MODE == TC_MODE_STEP) && updater && L >= Z0;
+      const int64_t nidx = (int64_t)L * d.plane + (int64_t)gj * d.nxp + gi;
+      if (upd) {
+        cn = d.C[nidx];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) uprev[c] = d.U_prev[c * d.comp + nidx];
-    }
+        for (int c = 0; c < 3; ++c) uprev[c] = d.U_prev[c * d.comp + nidx];
+      }
 
-    // (a) digitise plane L+2 while MMA(L) runs; prefetch plane L+3
-    bool okp = true;
-    if (L + 2 <= Llast + 1) {
-      okp = wait_plane(L + 2);
-    }
-    if (sync_abort(okp)) { aborted = true; break; }
-    if (L + 2 <= Llast + 1) digitise(L + 2);
-    if (L + 3 <= Llast + 1) issue_plane(L + 3);
+      // (a) digitise plane L+2 while MMA(L) runs; prefetch plane L+3
+      bool okp = true;
+      if (L + 2 <= Llast + 1) okp = wait_plane(L + 2);
+      if (sync_abort(okp)) { aborted = true; break; }
+      if (L + 2 <= Llast + 1) digitise(L + 2);
+      if (L + 3 <= Llast + 1) issue_plane(L + 3);
 
-    // (b) wait for MMA(L)
-    bool okm = mbar_wait(&bars[4], mma_phase);
-    mma_phase ^= 1u;
-    if (sync_abort(okm)) { aborted = true; break; }
-    tc_fence_after();
+      // (b) wait for this warp's tile of MMA(L)
+      const bool okm = mbar_wait(&bars[4 + tile], mma_phase);
+      mma_phase ^= 1u;
+      if (!okm) atomicExch(&misc[1], 1u);
+      tc_fence_after();
 
-    // (c) epilogue: per corner group (dy, dz), 5 stages x 12 columns
-    const TcMaterial mt = m >= 0 ? smat[m] : zero_mat;
-    const uint32_t tbase =
-        tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * kTileCols);
-    int64_t accL[3] = {0, 0, 0}, carry_next[3] = {0, 0, 0};
-    int64_t *ybuf0 = ybuf, *ybuf1 = ybuf + TC_EX * TC_EX * 3;
+      // (c) epilogue: per corner group (dy, dz), stages x 12 columns
+      const TcMaterial mt = m >= 0 ? smat[m] : zero_mat;
+      const int A1 = (int)(mt.A >> 31), A0 = (int)(mt.A & 0x7FFFFFFF);
+      const int B1 = (int)(mt.B >> 31), B0 = (int)(mt.B & 0x7FFFFFFF);
+      const uint32_t tbase =
+          tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * kTileCols);
+      int64_t own[3] = {0, 0, 0};  // this half's (dy = 1) corner sums
+      int64_t *yb_half = ybuf + half * (TC_EX * TC_EX * 3);
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      int64_t pq[12];
+      for (int gg = 0; gg < 2; ++gg) {
+        const int g = 2 * half + gg;
+        uint32_t w[TC_MAX_STAGES][12];
 #pragma unroll
-      for (int i = 0; i < 12; ++i) pq[i] = 0;
-      for (int s = TC_MAX_STAGES - 1; s >= s_lo; --s) {
-        uint32_t w[12];
-        const uint32_t ta = tbase + (uint32_t)(s * TC_N + 12 * g);
-        tmem_ld4(ta + 0, w[0], w[1], w[2], w[3]);
-        tmem_ld4(ta + 4, w[4], w[5], w[6], w[7]);
-        tmem_ld4(ta + 8, w[8], w[9], w[10], w[11]);
+        for (int s = 0; s < TC_MAX_STAGES; ++s) {
+          if constexpr (s_lo > 0) {
+            if (s < s_lo) {  // dropped low digit: a zero partial product
+#pragma unroll
+              for (int i = 0; i < 12; ++i) w[s][i] = TC_MAGIC_BITS;
+              continue;
+            }
+          }
+          const uint32_t ta = tbase + (uint32_t)(s * TC_N + 12 * g);
+          tmem_ld4(ta + 0, w[s][0], w[s][1], w[s][2], w[s][3]);
+          tmem_ld4(ta + 4, w[s][4], w[s][5], w[s][6], w[s][7]);
+          tmem_ld4(ta + 8, w[s][8], w[s][9], w[s][10], w[s][11]);
+        }
         tmem_wait_ld();
+        int64_t pq[12];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) pq[i] = pq[i] * 2048 + (int64_t)acc_to_int(w[i]);
+        for (int i = 0; i < 12; ++i) pq[i] = recombine5(w[0][i], w[1][i], w[2][i], w[3][i], w[4][i]);
+        const int dy = g & 1, dz = g >> 1;
+        if constexpr (MODE == TC_MODE_PARTIALS) {
+          if (elem_xy && L >= 0 && L < d.nz) {
+            const int64_t e = (int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L);
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+              const int a = dx + 2 * dy + 4 * dz;
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                d.partials_out[e * 48 + 3 * a + c] = pq[6 * dx + c];
+                d.partials_out[e * 48 + 24 + 3 * a + c] = pq[6 * dx + 3 + c];
+              }
+            }
+          }
+        } else {
+          // material: t = (P A + Q B) / 2^63 in the mesh-wide unit
+          int64_t f0[3], f1[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            f0[c] = mul2_hi63(pq[c], pq[3 + c], A1, A0, B1, B0);
+            f1[c] = mul2_hi63(pq[6 + c], pq[9 + c], A1, A0, B1, B0);
+          }
+          // x reduction: node (ei+1) gets dx=1 of element ei and dx=0 of ei+1
+          int64_t v[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int64_t nb = __shfl_down_sync(0xffffffffu, f0[c], 1);
+            v[c] = f1[c] + (ei < TC_EX - 1 ? nb : 0);
+          }
+          if (dy == 0) {
+            int64_t *yb = yb_half + (ej * TC_EX + ei) * 3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) yb[c] = v[c];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) own[c] = v[c];
+          }
+        }
       }
-      if (s_lo > 0) {
+      // (d) TMEM reads done; digit writes visible to the tensor core; MMA(L+1)
+      tc_fence_before();
+      fence_async_smem();
+      if (sync_abort(true)) { aborted = true; break; }
+      if (L + 1 <= Llast) issue_mma(L + 1);
+      if constexpr (MODE == TC_MODE_PARTIALS) continue;
+
+      // (e) y reduction from the shared buffer.  Half 1 holds the forces of
+      // layer L on plane L+1 and hands them to half 0 for the next layer through
+      // the double-buffered carry; half 0 completes plane L.
+      if (ej < TC_EX - 1) {
+        const int64_t *yv = yb_half + ((ej + 1) * TC_EX + ei) * 3;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) pq[i] *= (int64_t)1 << (TC_DIGIT_BITS * s_lo);
+        for (int c = 0; c < 3; ++c) own[c] += yv[c];
       }
-      if (MODE == TC_MODE_PARTIALS) {
-        if (gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && L >= 0 && L < d.nz) {
-          const int64_t e = (int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L);
-          const int dy = g & 1, dz = g >> 1;
+      int64_t *cb_next = cbuf + ((L + 1) & 1) * (TC_EX * TC_EX * 3) + (ej * TC_EX + ei) * 3;
+      const int64_t *cb_cur = cbuf + (L & 1) * (TC_EX * TC_EX * 3) + (ej * TC_EX + ei) * 3;
+      if (half == 1) {
 #pragma unroll
-          for (int dx = 0; dx < 2; ++dx) {
-            const int a = dx + 2 * dy + 4 * dz;
+        for (int c = 0; c < 3; ++c) cb_next[c] = own[c];
+        continue;
+      }
+      int64_t S[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              d.partials_out[e * 48 + 3 * a + c] = pq[6 * dx + c];
-              d.partials_out[e * 48 + 24 + 3 * a + c] = pq[6 * dx + 3 + c];
+      for (int c = 0; c < 3; ++c) S[c] = (L == Lfirst ? 0 : cb_cur[c]) + own[c];
+
+      // (f) update / output of node (gi, gj, L)
+      if (own_xy && L >= Z0) {
+        if (MODE == TC_MODE_KU) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) d.S_out[c * d.comp + nidx] = S[c];
+        } else if (MODE == TC_MODE_STEP) {
+          const int64_t *ucur = uslot + (L & 3) * (kUSlotStride / 8);
+          const bool is_src = (nidx == d.src_node);
+          int64_t unew[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int64_t u0 =
+                shr_round(ucur[(c * TC_NODES + ej + 1) * TC_BOXX + ei + 1 + xo], P.rs);
+            const int64_t um = shr_round(uprev[c], P.rs + P.rs_prev);
+            const __int128 prod = (__int128)S[c] * (__int128)cn;
+            int64_t du;
+            if (P.R > 0) {
+              const int R = min(P.R, 126);
+              du = (int64_t)((prod + ((__int128)1 << (R - 1))) >> R);
+            } else {  // the state is being scaled up: exact left shift
+              du = (int64_t)(prod << min(-P.R, 63));
+            }
+            int64_t un = 2 * u0 - um - du;
+            if (is_src) un += P.dU_src[c];
+            if (cn == 0) un = 0;  // fixed or massless node
+            unew[c] = un;
+            d.U_next[c * d.comp + nidx] = un;
+            // the slot bounds u^{n+1} and u^n (both in the new units)
+            or_acc |= (unsigned long long)(un < 0 ? -un : un) |
+                      (unsigned long long)(u0 < 0 ? -u0 : u0);
+          }
+          for (int r = 0; r < nrec; ++r) {
+            const TcRecv rv = srecv[r];
+            if (rv.ei == ei && rv.ej == ej && rv.k == L) {
+              double *out = d.traces + (P.trace_row * d.n_rec + rv.r) * 3;
+#pragma unroll
+              for (int c = 0; c < 3; ++c) out[c] = ldexp((double)unew[c], -P.F);
             }
           }
         }
-        continue;
-      }
-      // material: t = (P A + Q B) / 2^64, then to the common unit
-      int64_t f0[3], f1[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        int64_t t0 = __mul64hi(pq[c], mt.A) + __mul64hi(pq[3 + c], mt.B);
-        int64_t t1 = __mul64hi(pq[6 + c], mt.A) + __mul64hi(pq[9 + c], mt.B);
-        f0[c] = shr_round(t0, mt.shift);
-        f1[c] = shr_round(t1, mt.shift);
-      }
-      // x reduction: node (ei+1) gets dx=1 of element ei and dx=0 of ei+1
-      int64_t v[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        int64_t nb = __shfl_down_sync(0xffffffffu, f0[c], 1);
-        v[c] = f1[c] + (ei < TC_EX - 1 ? nb : 0);
-      }
-      const int dy = g & 1, dz = g >> 1;
-      if (dy == 0) {
-        int64_t *yb = (dz == 0 ? ybuf0 : ybuf1) + (ej * TC_EX + ei) * 3;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) yb[c] = v[c];
-      } else if (dz == 0) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) accL[c] = v[c];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) carry_next[c] = v[c];
       }
     }
-    // (d) TMEM reads done; digit writes visible to the tensor core; issue MMA(L+1)
-    tc_fence_before();
-    fence_async_smem();
-    __syncthreads();
-    if (L + 1 <= Llast) issue_mma(L + 1);
-    if (MODE == TC_MODE_PARTIALS) continue;
-
-    // (e) y reduction from the shared buffer, then the z carry
-    if (ej < TC_EX - 1) {
-      const int64_t *y0 = ybuf0 + ((ej + 1) * TC_EX + ei) * 3;
-      const int64_t *y1 = ybuf1 + ((ej + 1) * TC_EX + ei) * 3;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        accL[c] += y0[c];
-        carry_next[c] += y1[c];
-      }
-    }
-    int64_t S[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      S[c] = carry[c] + accL[c];
-      carry[c] = carry_next[c];
-    }
-
-    // (f) update / output of node (gi, gj, L)
-    if (own_xy && L >= Z0) {
-      if (MODE == TC_MODE_KU) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) d.S_out[c * d.comp + nidx] = S[c];
-      } else if (MODE == TC_MODE_STEP) {
-        const int64_t *ucur = uslot + (L & 3) * (kUSlotStride / 8);
-        const bool is_src = (nidx == d.src_node);
-        int64_t unew[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const int64_t u0 = shr_round(ucur[(c * TC_NODES + ej + 1) * TC_BOXX + ei + 1 + xo], P.rs);
-          const int64_t um = shr_round(uprev[c], P.rs + P.rs_prev);
-          const __int128 prod = (__int128)S[c] * (__int128)cn;
-          int64_t du;
-          if (P.R > 0) {
-            const int R = min(P.R, 126);
-            du = (int64_t)((prod + ((__int128)1 << (R - 1))) >> R);
-          } else {  // the state is being scaled up: exact left shift
-            du = (int64_t)(prod << min(-P.R, 63));
-          }
-          int64_t un = 2 * u0 - um - du;
-          if (is_src) un += P.dU_src[c];
-          if (cn == 0) un = 0;  // fixed or massless node
-          unew[c] = un;
-          d.U_next[c * d.comp + nidx] = un;
-          // the slot bounds u^{n+1} and u^n (both in the new units)
-          or_acc |= (unsigned long long)(un < 0 ? -un : un) | (unsigned long long)(u0 < 0 ? -u0 : u0);
-        }
-        for (int r = 0; r < nrec; ++r) {
-          const TcRecv rv = srecv[r];
-          if (rv.ei == ei && rv.ej == ej && rv.k == L) {
-            double *out = d.traces + (P.trace_row * d.n_rec + rv.r) * 3;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) out[c] = ldexp((double)unew[c], -P.F);
-          }
-        }
-      }
-    }
+    __syncthreads();  // srecv and the U slots are reused by the next segment
   }
 
   // ---- teardown -------------------------------------------------------------
@@ -599,7 +675,7 @@ __global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist,
   }
   const int F_new = F_old - rs;
   const int shq = max(0, b - TC_QBITS);
-  const int R = (int)persist[4] + rs - shq - 64;
+  const int R = (int)persist[4] + rs - shq - 63;
   TcStepParams p;
   p.step = n;
   p.trace_row = trace_on ? persist[2] : -1;
@@ -630,24 +706,39 @@ cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t 
   return cudaGetLastError();
 }
 
+template <int MODE, int S>
+static cudaError_t set_attr() {
+  return cudaFuncSetAttribute(tc_step_kernel<MODE, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kSmemBytes);
+}
+
+template <int MODE>
+static cudaError_t set_attr_all() {
+  cudaError_t e;
+  if ((e = set_attr<MODE, 1>()) != cudaSuccess) return e;
+  if ((e = set_attr<MODE, 2>()) != cudaSuccess) return e;
+  if ((e = set_attr<MODE, 3>()) != cudaSuccess) return e;
+  if ((e = set_attr<MODE, 4>()) != cudaSuccess) return e;
+  return set_attr<MODE, 5>();
+}
+
 cudaError_t tc_prepare() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(tc_step_kernel<TC_MODE_STEP>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(tc_step_kernel<TC_MODE_KU>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
-      cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(tc_step_kernel<TC_MODE_PARTIALS>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if ((e = set_attr_all<TC_MODE_STEP>()) != cudaSuccess) return e;
+  if ((e = set_attr_all<TC_MODE_KU>()) != cudaSuccess) return e;
+  return set_attr_all<TC_MODE_PARTIALS>();
 }
 
 template <int MODE>
 static cudaError_t launch_mode(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap) {
-  const int items = d.tiles_x * d.tiles_y * d.tiles_z;
-  tc_step_kernel<MODE><<<items, TC_THREADS, kSmemBytes, s>>>(*tmap, d);
+  const dim3 grid(d.n_ctas), block(TC_THREADS);
+  switch (d.stages) {
+    case 1: tc_step_kernel<MODE, 1><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
+    case 2: tc_step_kernel<MODE, 2><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
+    case 3: tc_step_kernel<MODE, 3><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
+    case 4: tc_step_kernel<MODE, 4><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
+    default: tc_step_kernel<MODE, 5><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
+  }
   return cudaGetLastError();
 }
 
