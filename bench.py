@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit voxel FE wave step (arXiv 2404.13683, OVFEM).
+
+One bench "step" is one time step of the whole hot path -- f = K u over every
+element (integer-split tensor-core products) plus the central-difference
+update, source and receiver recording -- on the 128 x 128 x 64 layered model
+with 20 ellipsoidal inclusions (1,048,576 elements, ``workloads.config2``).
+
+Prints one JSON line (rank 0).  ``value`` is element*steps/s over all ranks;
+ranks run independent replicas (the path needs no exchange on one GPU).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
+same workload and prints the same line with ``"impl": "reference"``.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "element·steps/s, INT8-TC vs FP64 path on 1 GB300 at ≤1e-6 rel trace error"
+UNIT = "element*steps/s"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+PROFILE_TXT = os.path.join(ROOT, "profiles", "tc_step_kernel_config2_128x128x64.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2404_13683_gb300", "csrc", "vfe_tc.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--stages", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def workload_config(mesh, stages, path_name):
+    nx, ny, nz = mesh["shape"]
+    return {"workload": "%s layered ground + 20 inclusions, OVFEM, %s path" % (mesh["name"], path_name),
+            "elements": nx * ny * nz, "nodes": (nx + 1) * (ny + 1) * (nz + 1),
+            "materials": int(len(mesh["material_table"])), "receivers": int(len(mesh["receivers"])),
+            "tc_digit_stages": stages, "tc_digit_bits": 11,
+            "l2": "flushed (512 MiB write) between timed steps", "step": "one time step"}
+
+
+# --------------------------------------------------------------------------
+# clocks (nvidia-smi sampled during the timed region)
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join("/tmp", "vfe_clocks_%d_%d.csv" % (os.getpid(), gpu))
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 7:
+                    rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# roofline bookkeeping for the dominant kernel (tc_step_kernel)
+# --------------------------------------------------------------------------
+def algorithmic_bytes_per_step(mesh):
+    """HBM bytes one time step must move at minimum: read u^n, u^{n-1} and the
+    per-node update multiplier, write u^{n+1} (3 x int64 each), read each
+    element's int32 material id."""
+    nx, ny, nz = mesh["shape"]
+    nodes = (nx + 1) * (ny + 1) * (nz + 1)
+    return nodes * (24 + 24 + 24 + 8) + nx * ny * nz * 4
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    try:
+        with open(PROFILE_TXT) as f:
+            text = f.read()
+        with open(KERNEL_SRC, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------
+# our implementation
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2404_13683_gb300 import build as vbuild
+    if rank == 0:
+        vbuild.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2404_13683_gb300 import vfe, workloads as W
+
+    mesh = W.config2()
+    ne = int(mesh["material_ids"].size)
+    # a dedicated stream: the library launches on it and the events are
+    # recorded on it (torch's default stream is the legacy NULL stream)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed_steps(m, steps, warmup):
+        for _ in range(warmup):
+            m.step(1)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()                       # evict L2 between timed steps
+            ev[k][0].record(stream)
+            m.step(1)                           # prologue + tc_step_kernel
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        m.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return float(np.sum(ms)), ms
+
+    # --- the TC path (headline)
+    m = vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stages=args.stages, stream=stream.cuda_stream,
+                 device=local)
+    with ClockSampler(local) as clk:
+        total_ms, per = timed_steps(m, args.steps, args.warmup)
+    clocks = clk.summary()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * ne * args.steps / (total_ms * 1e-3)
+    m.close()
+
+    # --- e2e: the public API on host buffers -- each step is vfe_step(1)
+    # followed by the device-to-host read of that step's receiver row
+    # (synchronous); the model itself is uploaded by vfe_create_mesh.
+    m = vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stages=args.stages, device=local)
+    row = np.zeros((1, m.n_rec, 3))
+    for k in range(args.warmup):
+        m.step(1)
+        vfe.vfe_get_trace_rows(m.handle, k, 1, m.n_rec, row)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        m.step(1)
+        vfe.vfe_get_trace_rows(m.handle, args.warmup + k, 1, m.n_rec, row)
+    e2e_s = time.perf_counter() - t0
+    m.close()
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * ne * args.steps / float(te.item())
+
+    # --- the plain FP64 CUDA-core path on the same workload, and the trace
+    # agreement of the two GPU paths over the same steps
+    cfg = workload_config(mesh, args.stages, "TC (exact 11-bit integer digits on tcgen05)")
+    if not args.no_fp64:
+        nf = max(3, min(args.steps, 20))
+        mf = vfe.Mesh(mesh, path=vfe.VFE_PATH_FP64, stream=stream.cuda_stream, device=local)
+        f_ms, _ = timed_steps(mf, nf, min(args.warmup, 3))
+        mf.close()
+        f_value = ne * nf / (f_ms * 1e-3)
+        cfg["fp64_path_value"] = f_value
+        cfg["speedup_vs_fp64_path"] = (value / world) / f_value
+        # the workload's full 2,000 steps on both paths from rest (untimed)
+        nt = int(mesh["nsteps"])
+        trs = []
+        for path in (vfe.VFE_PATH_TC, vfe.VFE_PATH_FP64):
+            mp = vfe.Mesh(mesh, path=path, stages=args.stages, stream=stream.cuda_stream,
+                          device=local)
+            mp.step(nt)
+            trs.append(mp.traces())
+            mp.close()
+        num = float(np.linalg.norm(trs[0] - trs[1]))
+        den = float(np.linalg.norm(trs[1]))
+        cfg["trace_rel_l2_tc_vs_fp64_path"] = num / den if den > 0 else None
+        cfg["trace_steps_compared"] = nt
+
+    # --- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    abytes = algorithmic_bytes_per_step(mesh)
+    achieved = abytes / (ms_step * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+            "frac": achieved / float(peaks["hbm_gbs"]), "traffic": profiled_traffic(),
+            "algorithmic_bytes_per_launch": abytes, "peak_source": peak_src,
+            "kernel": "tc_step_kernel (duration includes the one-thread prologue launch)"}
+
+    # --- the CPU oracle on a bounded sample (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mesh, target_s=15.0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int64", "data": "synthetic", "config": cfg,
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": int(len(mesh["receivers"]) * 3 * 8),
+                        "note": "per step: vfe_step(1) + synchronous read of that step's "
+                                "receiver row; the model is uploaded once by vfe_create_mesh "
+                                "and the source is evaluated on the device"},
+                "gpu_launches": 2 * args.steps, "clocks": clocks,
+                "parallelism": "replicas x%d" % world if world > 1 else "1 GPU"}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# the CPU oracle (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------
+def _oracle_step_runner(mesh):
+    import oracle
+    from paper_2404_13683_gb300 import workloads as W
+    oracle.build()
+    dt = oracle.dt(0, mesh, 0.5)
+    s = mesh["source"]
+    src = {"node": W.source_node(mesh), "dir": s["dir"], "f0": s["f0"], "t0": s["t0"],
+           "amp": s["amp"]}
+    rec = W.receiver_nodes(mesh)
+    nn = (mesh["shape"][0] + 1) * (mesh["shape"][1] + 1) * (mesh["shape"][2] + 1)
+    state = {"u": np.zeros(3 * nn), "um": np.zeros(3 * nn)}
+
+    def step(n):
+        _, u, um = oracle.run(0, mesh, dt, n, source=src, receivers=rec, u0=state["u"],
+                              um1=state["um"], return_state=True)
+        state["u"], state["um"] = u, um
+    return step
+
+
+def cpu_baseline(mesh, target_s=15.0):
+    step = _oracle_step_runner(mesh)
+    ne = int(mesh["material_ids"].size)
+    t0 = time.perf_counter()
+    step(1)
+    one = time.perf_counter() - t0
+    n = max(1, int(target_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    step(n)
+    el = time.perf_counter() - t0
+    return {"value": ne * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d time steps of the full %s model (element-by-element FP64 K u and "
+                      "update, plain C, one thread)" % (n, mesh["name"])}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2404_13683_gb300 import workloads as W
+    mesh = W.config2()
+    ne = int(mesh["material_ids"].size)
+    step = _oracle_step_runner(mesh)
+    for _ in range(args.warmup):
+        step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(1)
+    el = time.perf_counter() - t0
+    value = ne * args.steps / el
+    cfg = workload_config(mesh, args.stages, "FP64 CPU oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step = one full time step of %s" % mesh["name"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

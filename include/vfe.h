@@ -78,8 +78,9 @@ int vfe_destroy(vfe_mesh *mesh);
 
 /* Point force at node (i,j,k): F(t) = amp * ricker(t; f0, t0) * dir with the
  * Ricker wavelet (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), applied
- * as F^n at t = n dt (Section 3 uses an impulse force in z).  t0 <= 0 selects
- * t0 = 1/f0.  Forces at a fixed or massless node are ignored. */
+ * as F^n at t = n dt (Section 3 uses an impulse force in z), evaluated on
+ * the device each step.  t0 <= 0 selects t0 = 1/f0.  Forces at a fixed or
+ * massless node are ignored. */
 int vfe_set_source(vfe_mesh *mesh, int i, int j, int k, const double dir[3],
                    double f0_hz, double t0_s, double amp);
 
@@ -104,6 +105,11 @@ int vfe_synchronize(vfe_mesh *mesh);
 /* Copy the traces recorded since vfe_set_receivers: out[s][r][3] FP64 for
  * s < *n_steps_out (out may be NULL to query the count only).  Synchronous. */
 int vfe_get_traces(vfe_mesh *mesh, double *out, int64_t *n_steps_out);
+
+/* Copy trace rows [first, first+count) (same layout as vfe_get_traces) after
+ * the work queued so far has finished.  Lets a caller read each step's
+ * receiver values as they are produced.  Synchronous. */
+int vfe_get_trace_rows(vfe_mesh *mesh, int64_t first, int64_t count, double *out);
 
 /* Time step in use, number of nodes, and steps taken since creation. */
 int vfe_get_dt(vfe_mesh *mesh, double *dt);

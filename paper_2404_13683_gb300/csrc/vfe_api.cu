@@ -3,7 +3,7 @@
 // Host responsibilities: argument validation, element matrices (closed form
 // of Section 2's element stiffness), node masses, the CFL step, the
 // fixed-point scales of the tensor-core path, TMA tensor maps, work
-// decomposition, receivers, the Ricker source series, and stepping through
+// decomposition, receivers, the Ricker source parameters, and stepping through
 // captured CUDA graphs.  Every step of the hot path runs in the kernels of
 // vfe_tc.cu / vfe_fp64.cu; there is no CPU fallback.
 #include <cuda_fp16.h>
@@ -94,11 +94,6 @@ double max_eigenvalue(const double *K) {
   return lam;
 }
 
-double ricker(double t, double f0, double t0) {
-  const double a = M_PI * M_PI * f0 * f0 * (t - t0) * (t - t0);
-  return (1.0 - 2.0 * a) * std::exp(-a);
-}
-
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -117,7 +112,6 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-const int64_t kSeriesChunk = 8192;
 
 }  // namespace
 
@@ -140,7 +134,6 @@ struct vfe_mesh {
 
   int32_t *d_mat = nullptr;
   int *d_status = nullptr;
-  double *d_series = nullptr;
   double *d_traces = nullptr;
   int64_t trace_cap = 0, trace_rows = 0;
   int n_rec = 0;
@@ -235,15 +228,20 @@ static F64Device f64_device(const vfe_mesh *m, int cur) {
 // one time step on the stream (prologue + kernel) starting from state cur
 static int enqueue_step(vfe_mesh *m, int cur) {
   const int trace_on = m->n_rec > 0 ? 1 : 0;
+  TcSource src;
+  src.dt = m->dt;
+  src.f0 = m->f0;
+  src.t0 = m->t0;
+  for (int c = 0; c < 3; ++c) src.dir[c] = m->src_dir[c];
   if (m->opt.path == VFE_PATH_TC) {
-    CUDA_TRY(tc_launch_prologue_ex(m->stream, m->d_tcparams, m->d_tcpersist, m->d_series, m->d_or,
-                                   m->src_scale, m->src_dir, m->has_src ? 1 : 0, trace_on,
-                                   m->d_status));
+    src.amp_scale = m->amp * m->src_scale;
+    CUDA_TRY(tc_launch_prologue_ex(m->stream, m->d_tcparams, m->d_tcpersist, src, m->d_or,
+                                   m->has_src ? 1 : 0, trace_on, m->d_status));
     TcDevice d = tc_device(m, cur);
     CUDA_TRY(tc_launch_step(m->stream, d, &m->tmap[cur], TC_MODE_STEP));
   } else {
-    double amp_dir[3] = {m->amp * m->src_dir[0], m->amp * m->src_dir[1], m->amp * m->src_dir[2]};
-    CUDA_TRY(f64_launch_prologue(m->stream, m->d_f64params, m->d_f64persist, m->d_series, amp_dir,
+    src.amp_scale = m->amp;
+    CUDA_TRY(f64_launch_prologue(m->stream, m->d_f64params, m->d_f64persist, src,
                                  m->has_src ? 1 : 0, trace_on));
     F64Device d = f64_device(m, cur);
     CUDA_TRY(f64_launch_step(m->stream, d, m->d_f64params, 0));
@@ -302,7 +300,7 @@ int vfe_destroy(vfe_mesh *m) {
   cudaSetDevice(m->device);
   if (m->stream) cudaStreamSynchronize(m->stream);
   invalidate_graphs(m);
-  void *ptrs[] = {m->d_mat, m->d_status, m->d_series, m->d_traces, m->d_u[0], m->d_u[1],
+  void *ptrs[] = {m->d_mat, m->d_status, m->d_traces, m->d_u[0], m->d_u[1],
                   m->d_dt2m, m->d_K, m->d_recnodes, m->d_f64params, m->d_f64persist,
                   m->d_U[0], m->d_U[1], m->d_C, m->d_Bop, m->d_mats, m->d_recv,
                   m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist, m->d_segs,
@@ -423,15 +421,13 @@ int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_id
     }
     cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
     if ((e = cudaMalloc(&m->d_mat, sizeof(int32_t) * m->ne)) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_status, sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&m->d_series, sizeof(double) * kSeriesChunk)) != cudaSuccess) {
+        (e = cudaMalloc(&m->d_status, sizeof(int))) != cudaSuccess) {
       rc = fail(VFE_ENOMEM, "device allocation: %s", cudaGetErrorString(e));
       break;
     }
     if ((e = cudaMemcpy(m->d_mat, m->mat.data(), sizeof(int32_t) * m->ne,
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(m->d_status, 0, sizeof(int))) != cudaSuccess ||
-        (e = cudaMemset(m->d_series, 0, sizeof(double) * kSeriesChunk)) != cudaSuccess) {
+        (e = cudaMemset(m->d_status, 0, sizeof(int))) != cudaSuccess) {
       rc = fail(VFE_ECUDA, "device upload: %s", cudaGetErrorString(e));
       break;
     }
@@ -744,42 +740,22 @@ int vfe_step(vfe_mesh *m, int n) {
   cudaSetDevice(m->device);
   int rc = ensure_trace_capacity(m, m->trace_rows + n);
   if (rc != VFE_OK) return rc;
-  int64_t done = 0;
-  std::vector<double> series;
-  while (done < n) {
-    const int64_t chunk = std::min<int64_t>(n - done, kSeriesChunk);
-    // source samples for steps [steps, steps + chunk); FP64 path folds amp in
-    // the prologue, the TC path folds dt^2/m there as well
-    series.assign(chunk, 0.0);
-    if (m->has_src)
-      for (int64_t s = 0; s < chunk; ++s) {
-        const double t = (double)(m->steps + s) * m->dt;
-        series[s] = (m->opt.path == VFE_PATH_TC ? m->amp : 1.0) * ricker(t, m->f0, m->t0);
-      }
-    CUDA_TRY(cudaStreamSynchronize(m->stream));
-    CUDA_TRY(cudaMemcpy(m->d_series, series.data(), sizeof(double) * chunk,
-                        cudaMemcpyHostToDevice));
-    const int64_t base = m->steps;
-    int64_t *persist = m->opt.path == VFE_PATH_TC ? m->d_tcpersist + 3 : m->d_f64persist + 2;
-    CUDA_TRY(cudaMemcpy(persist, &base, sizeof(int64_t), cudaMemcpyHostToDevice));
-    int64_t left = chunk;
-    while (left >= 2) {
-      rc = ensure_graph(m, m->cur);
-      if (rc != VFE_OK) return rc;
-      CUDA_TRY(cudaGraphLaunch(m->graph[m->cur], m->stream));
-      left -= 2;
-      m->steps += 2;
-      if (m->n_rec) m->trace_rows += 2;
-    }
-    if (left == 1) {
-      rc = enqueue_step(m, m->cur);
-      if (rc != VFE_OK) return rc;
-      m->cur = 1 - m->cur;
-      m->steps += 1;
-      if (m->n_rec) m->trace_rows += 1;
-    }
-    done += chunk;
+  // pairs of steps replay a captured two-step graph; the source term, scales
+  // and trace rows live in device memory, so the graph is reusable
+  int64_t left = n;
+  while (left >= 2) {
+    rc = ensure_graph(m, m->cur);
+    if (rc != VFE_OK) return rc;
+    CUDA_TRY(cudaGraphLaunch(m->graph[m->cur], m->stream));
+    left -= 2;
   }
+  if (left == 1) {
+    rc = enqueue_step(m, m->cur);
+    if (rc != VFE_OK) return rc;
+    m->cur = 1 - m->cur;
+  }
+  m->steps += n;
+  if (m->n_rec) m->trace_rows += n;
   return VFE_OK;
 }
 
@@ -799,6 +775,21 @@ int vfe_get_traces(vfe_mesh *m, double *out, int64_t *n_steps_out) {
     CUDA_TRY(cudaMemcpy(out, m->d_traces, sizeof(double) * 3 * m->n_rec * m->trace_rows,
                         cudaMemcpyDeviceToHost));
   return VFE_OK;
+}
+
+int vfe_get_trace_rows(vfe_mesh *m, int64_t first, int64_t count, double *out) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  if (first < 0 || count < 0 || (count > 0 && !out)) return fail(VFE_EINVAL, "bad row range");
+  cudaSetDevice(m->device);
+  if (first + count > m->trace_rows)
+    return fail(VFE_EINVAL, "rows [%lld, %lld) beyond the %lld recorded", (long long)first,
+                (long long)(first + count), (long long)m->trace_rows);
+  if (count == 0 || m->n_rec == 0) return VFE_OK;
+  CUDA_TRY(cudaMemcpyAsync(out, m->d_traces + first * 3 * m->n_rec,
+                           sizeof(double) * 3 * m->n_rec * count, cudaMemcpyDeviceToHost,
+                           m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  return check_status(m);
 }
 
 int vfe_get_dt(vfe_mesh *m, double *dt) {

@@ -15,18 +15,19 @@ struct F64StepParams {
   double src[3];
 };
 
-// persist[0] = step, [1] = trace rows, [2] = series base
-__global__ void f64_prologue_kernel(F64StepParams *p, int64_t *persist, const double *series,
-                                    double d0, double d1, double d2, int have_src, int trace_on) {
+// persist[0] = step, [1] = trace rows
+__global__ void f64_prologue_kernel(F64StepParams *p, int64_t *persist, TcSource sd, int have_src,
+                                    int trace_on) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int64_t n = persist[0];
   F64StepParams q;
   q.step = n;
   q.trace_row = trace_on ? persist[1] : -1;
-  const double fv = have_src ? series[n - persist[2]] : 0.0;
-  q.src[0] = fv * d0;
-  q.src[1] = fv * d1;
-  q.src[2] = fv * d2;
+  // F^n = amp ricker(n dt) dir
+  const double fv = have_src ? sd.amp_scale * ricker_wavelet((double)n * sd.dt, sd.f0, sd.t0) : 0.0;
+  q.src[0] = fv * sd.dir[0];
+  q.src[1] = fv * sd.dir[1];
+  q.src[2] = fv * sd.dir[2];
   *p = q;
   persist[0] = n + 1;
   if (trace_on) persist[1] += 1;
@@ -107,10 +108,9 @@ static cudaError_t f64_launch(cudaStream_t s, const F64Device &d, const F64StepP
 size_t f64_params_bytes() { return sizeof(F64StepParams); }
 
 cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,
-                                const double *series, const double dir[3], int have_src,
-                                int trace_on) {
-  f64_prologue_kernel<<<1, 32, 0, s>>>(reinterpret_cast<F64StepParams *>(params), persist, series,
-                                       dir[0], dir[1], dir[2], have_src, trace_on);
+                                const TcSource &src, int have_src, int trace_on) {
+  f64_prologue_kernel<<<1, 32, 0, s>>>(reinterpret_cast<F64StepParams *>(params), persist, src,
+                                       have_src, trace_on);
   return cudaGetLastError();
 }
 

@@ -103,19 +103,31 @@ struct F64Device {
   double *f_out;          // K u mode output
 };
 
+// Ricker point source (Section 3 applies an impulse force in z):
+// F(t) = amp_scale * (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2) * dir,
+// evaluated by the per-step prologue at t = n dt.  amp_scale is amp on the
+// FP64 path and amp * dt^2 / m(source node) on the TC path.
+struct TcSource {
+  double amp_scale, dt, f0, t0;
+  double dir[3];
+};
+
+__device__ __forceinline__ double ricker_wavelet(double t, double f0, double t0) {
+  const double a = 9.869604401089358 * f0 * f0 * (t - t0) * (t - t0);  // pi^2 f0^2 (t-t0)^2
+  return (1.0 - 2.0 * a) * exp(-a);
+}
+
 // launch helpers implemented in the .cu files ---------------------------------
 enum { TC_MODE_STEP = 0, TC_MODE_KU = 1, TC_MODE_PARTIALS = 2 };
 int tc_smem_bytes();
 cudaError_t tc_prepare();
 cudaError_t f64_prepare();
 cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t *persist,
-                                  const double *series, unsigned long long *or_slots,
-                                  double src_scale, const double dir[3], int have_src,
+                                  const TcSource &src, unsigned long long *or_slots, int have_src,
                                   int trace_on, int *status);
 cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
 
 size_t f64_params_bytes();
 cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,
-                                const double *series, const double dir[3], int have_src,
-                                int trace_on);
+                                const TcSource &src, int have_src, int trace_on);
 cudaError_t f64_launch_step(cudaStream_t s, const F64Device &d, const void *params, int mode);

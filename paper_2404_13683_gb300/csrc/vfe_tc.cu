@@ -639,12 +639,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ---------------------------------------------------------------------------
 // per-step prologue: rescale decision, digit shift, source increment
 // ---------------------------------------------------------------------------
-// persist[0] = F of u^n, [1] = step, [2] = trace rows, [3] = series base,
-// [4] = eC + e_ref, [5] = shift of the last step (u^{n-1} has F + [5])
-__global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist,
-                                   const double *series, unsigned long long *or_slots,
-                                   double src_scale, double dir0, double dir1, double dir2,
-                                   int have_src, int trace_on, int *status) {
+// persist[0] = F of u^n, [1] = step, [2] = trace rows, [4] = eC + e_ref,
+// [5] = shift of the last step (u^{n-1} has F + [5])
+__global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist, TcSource src_desc,
+                                   unsigned long long *or_slots, int have_src, int trace_on,
+                                   int *status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int64_t n = persist[1];
   const int F_old = (int)persist[0];
@@ -656,8 +655,10 @@ __global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist,
   int bs = 0;
   bool bs_valid = false;
   if (have_src) {
-    const double fv = series[n - persist[3]] * src_scale;
-    const double dir[3] = {dir0, dir1, dir2};
+    // F^n = amp ricker(n dt) dir, scaled by dt^2 / m of the source node
+    const double fv = src_desc.amp_scale * ricker_wavelet((double)n * src_desc.dt, src_desc.f0,
+                                                          src_desc.t0);
+    const double dir[3] = {src_desc.dir[0], src_desc.dir[1], src_desc.dir[2]};
     double mx = 0.0;
     for (int c = 0; c < 3; ++c) {
       src[c] = fv * dir[c];
@@ -698,11 +699,9 @@ __global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist,
 int tc_smem_bytes() { return kSmemBytes; }
 
 cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t *persist,
-                                  const double *series, unsigned long long *or_slots,
-                                  double src_scale, const double dir[3], int have_src,
+                                  const TcSource &src, unsigned long long *or_slots, int have_src,
                                   int trace_on, int *status) {
-  tc_prologue_kernel<<<1, 32, 0, s>>>(params, persist, series, or_slots, src_scale, dir[0],
-                                      dir[1], dir[2], have_src, trace_on, status);
+  tc_prologue_kernel<<<1, 32, 0, s>>>(params, persist, src, or_slots, have_src, trace_on, status);
   return cudaGetLastError();
 }
 

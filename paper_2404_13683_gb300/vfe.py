@@ -32,6 +32,7 @@ EXPORTS = (
     "vfe_set_receivers", "vfe_internal_force", "vfe_step", "vfe_synchronize",
     "vfe_get_traces", "vfe_get_dt", "vfe_get_sizes", "vfe_get_step_count",
     "vfe_get_state", "vfe_set_state", "vfe_last_error", "vfe_debug_tc_partials",
+    "vfe_get_trace_rows",
 )
 
 
@@ -77,6 +78,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_step.argtypes = [P, I]
     L.vfe_synchronize.argtypes = [P]
     L.vfe_get_traces.argtypes = [P, P, ctypes.POINTER(I64)]
+    L.vfe_get_trace_rows.argtypes = [P, I64, I64, P]
     L.vfe_get_dt.argtypes = [P, ctypes.POINTER(D)]
     L.vfe_get_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
     L.vfe_get_step_count.argtypes = [P, ctypes.POINTER(I64)]
@@ -172,6 +174,13 @@ def vfe_get_traces(mesh, n_rec=None):
     out = np.zeros((rows.value, n_rec, 3))
     if rows.value and n_rec:
         _check(load().vfe_get_traces(mesh, _p(out), ctypes.byref(rows)))
+    return out
+
+
+def vfe_get_trace_rows(mesh, first, count, n_rec, out=None):
+    if out is None:
+        out = np.zeros((count, n_rec, 3))
+    _check(load().vfe_get_trace_rows(mesh, int(first), int(count), _p(out)))
     return out
 
 
