@@ -134,6 +134,30 @@ int vfe_debug_tc_partials(vfe_mesh *mesh, const double *u, int n,
                           const int64_t *ids, int64_t *out, int *shift_out,
                           int *frac_bits_out);
 
+/* K u of the tensor-core path for callers that cannot allocate device memory:
+ * u and f are FP64 [nodes][3] host arrays as in vfe_internal_force, and the
+ * result agrees with it to the same FP64-level tolerance.  The paper has no
+ * counterpart to this entry point.
+ *
+ * Who needs it: code running inside a framework that owns the whole device
+ * memory pool, real-time loops where cudaMalloc's implicit synchronisation is
+ * not acceptable, and deployments that budget every byte at start-up.  The
+ * call performs no cudaMalloc, cudaFree or other allocating routine; all its
+ * temporaries live in one statically declared device array of
+ * VFE_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU loading the library holds
+ * until the process exits.  A mesh whose temporaries exceed the array (about
+ * 48 bytes per padded node, so up to roughly 1.3 M nodes) is rejected with
+ * VFE_EINVAL and a message giving both sizes.
+ *
+ * The first call on a device, with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it, so make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (each call clears what must start at zero); calls whose GPU
+ * work overlaps -- from several threads or streams -- race on it.  TC path
+ * only (VFE_ESTATE otherwise).  Synchronous on the mesh's stream. */
+#define VFE_NOALLOC_SCRATCH_BYTES (64u << 20)
+int vfe_internal_force_noalloc(vfe_mesh *mesh, const double *u, double *f);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1028,6 +1028,36 @@ int vfe_internal_force(vfe_mesh *m, const double *u, double *f) {
   return rc;
 }
 
+}  // extern "C"
+
+void vfe_set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+int vfe_mesh_view(vfe_mesh *m, VfeMeshView *v) {
+  if (!m || !v) return VFE_EINVAL;
+  v->nx = m->nx; v->ny = m->ny; v->nz = m->nz; v->nxp = m->nxp; v->nyp = m->nyp;
+  v->nn = m->nn; v->plane = m->plane; v->comp = m->comp;
+  v->e_ref = m->e_ref;
+  v->device = m->device;
+  v->tc = m->opt.path == VFE_PATH_TC ? 1 : 0;
+  v->stream = m->stream;
+  v->dev = tc_device(m, m->cur);
+  return VFE_OK;
+}
+
+CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return CUDA_ERROR_NOT_SUPPORTED;
+  cuuint64_t dims[4] = {(cuuint64_t)v.nxp, (cuuint64_t)v.nyp, (cuuint64_t)(v.nz + 1), 3};
+  cuuint64_t strides[3] = {(cuuint64_t)v.nxp * 8, (cuuint64_t)v.plane * 8, (cuuint64_t)v.comp * 8};
+  cuuint32_t box[4] = {TC_BOXX, TC_NODES, 1, 3};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, base, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+extern "C" {
+
 int vfe_debug_tc_partials(vfe_mesh *m, const double *u, int n, const int64_t *ids, int64_t *out,
                           int *shift_out, int *frac_bits_out) {
   if (!m || !u || (n > 0 && (!ids || !out))) return fail(VFE_EINVAL, "NULL argument");

@@ -117,6 +117,21 @@ __device__ __forceinline__ double ricker_wavelet(double t, double f0, double t0)
   return (1.0 - 2.0 * a) * exp(-a);
 }
 
+// read-only view of a mesh for code outside vfe_api.cu ------------------------
+struct VfeMeshView {
+  int nx, ny, nz, nxp, nyp;
+  int64_t nn, plane, comp;
+  int e_ref;
+  int device;
+  int tc;                 // 1 on the tensor-core path
+  cudaStream_t stream;
+  TcDevice dev;           // kernel arguments with the mesh's own pointers
+};
+int vfe_mesh_view(vfe_mesh *mesh, VfeMeshView *view);
+void vfe_set_last_error(const char *msg);  // message returned by vfe_last_error()
+// tensor map of a padded SoA int64 nodal array laid out like the state
+CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v);
+
 // launch helpers implemented in the .cu files ---------------------------------
 enum { TC_MODE_STEP = 0, TC_MODE_KU = 1, TC_MODE_PARTIALS = 2 };
 int tc_smem_bytes();

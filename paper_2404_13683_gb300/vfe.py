@@ -32,7 +32,7 @@ EXPORTS = (
     "vfe_set_receivers", "vfe_internal_force", "vfe_step", "vfe_synchronize",
     "vfe_get_traces", "vfe_get_dt", "vfe_get_sizes", "vfe_get_step_count",
     "vfe_get_state", "vfe_set_state", "vfe_last_error", "vfe_debug_tc_partials",
-    "vfe_get_trace_rows",
+    "vfe_get_trace_rows", "vfe_internal_force_noalloc",
 )
 
 
@@ -75,6 +75,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_set_source.argtypes = [P, I, I, I, P, D, D, D]
     L.vfe_set_receivers.argtypes = [P, I, P]
     L.vfe_internal_force.argtypes = [P, P, P]
+    L.vfe_internal_force_noalloc.argtypes = [P, P, P]
     L.vfe_step.argtypes = [P, I]
     L.vfe_synchronize.argtypes = [P]
     L.vfe_get_traces.argtypes = [P, P, ctypes.POINTER(I64)]
@@ -155,6 +156,16 @@ def vfe_internal_force(mesh, u):
         raise ValueError("u must have 3*n_nodes entries")
     f = np.empty_like(u)
     _check(load().vfe_internal_force(mesh, _p(u), _p(f)))
+    return f
+
+
+def vfe_internal_force_noalloc(mesh, u):
+    nn, _ = vfe_get_sizes(mesh)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    if u.size != 3 * nn:
+        raise ValueError("u must have 3*n_nodes entries")
+    f = np.empty_like(u)
+    _check(load().vfe_internal_force_noalloc(mesh, _p(u), _p(f)))
     return f
 
 
