@@ -166,6 +166,25 @@ def profiled_traffic():
 
 
 # --------------------------------------------------------------------------
+# replicas across ranks: each rank advances its own copy of the model, so the
+# job's throughput is the work of all ranks over the slowest rank's time
+# --------------------------------------------------------------------------
+def reduce_max(x, dist, device):
+    """Max of a per-rank float over all ranks (identity without a group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, elements, steps, seconds_max):
+    """element*steps/s of the whole job (weak scaling: fixed work per rank)."""
+    return world * elements * steps / seconds_max
+
+
+# --------------------------------------------------------------------------
 # our implementation
 # --------------------------------------------------------------------------
 def run_ours(args):
@@ -216,12 +235,9 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         total_ms, per = timed_steps(m, args.steps, args.warmup)
     clocks = clk.summary()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = reduce_max(total_ms, dist, "cuda")
     ms_step = total_ms / args.steps
-    value = world * ne * args.steps / (total_ms * 1e-3)
+    value = replica_throughput(world, ne, args.steps, total_ms * 1e-3)
     m.close()
 
     # --- e2e: the public API on host buffers -- each step is vfe_step(1)
@@ -240,10 +256,7 @@ def run_ours(args):
         vfe.vfe_get_trace_rows(m.handle, args.warmup + k, 1, m.n_rec, row)
     e2e_s = time.perf_counter() - t0
     m.close()
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * ne * args.steps / float(te.item())
+    e2e_value = replica_throughput(world, ne, args.steps, reduce_max(e2e_s, dist, "cuda"))
 
     # --- the plain FP64 CUDA-core path on the same workload, and the trace
     # agreement of the two GPU paths over the same steps

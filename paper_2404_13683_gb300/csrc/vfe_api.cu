@@ -210,6 +210,7 @@ static TcDevice tc_device(const vfe_mesh *m, int cur) {
   d.Bop = m->d_Bop; d.mats = m->d_mats; d.recv = m->d_recv; d.recv_off = m->d_recv_off;
   d.src_node = m->has_src ? tc_index(m, m->src_node) : -1;
   d.traces = m->d_traces; d.or_slots = m->d_or; d.status = m->d_status;
+  d.tiles_x = m->tiles_x; d.tiles_y = m->tiles_y;
   d.params = m->d_tcparams;
   return d;
 }
@@ -236,7 +237,8 @@ static int enqueue_step(vfe_mesh *m, int cur) {
   if (m->opt.path == VFE_PATH_TC) {
     src.amp_scale = m->amp * m->src_scale;
     CUDA_TRY(tc_launch_prologue_ex(m->stream, m->d_tcparams, m->d_tcpersist, src, m->d_or,
-                                   m->has_src ? 1 : 0, trace_on, m->d_status));
+                                   m->tiles_x * m->tiles_y, m->has_src ? 1 : 0, trace_on,
+                                   m->d_status));
     TcDevice d = tc_device(m, cur);
     CUDA_TRY(tc_launch_step(m->stream, d, &m->tmap[cur], TC_MODE_STEP));
   } else {
@@ -575,7 +577,8 @@ static int build_tc(vfe_mesh *m) {
   CUDA_TRY(cudaMalloc(&m->d_C, sizeof(int64_t) * C.size()));
   CUDA_TRY(cudaMalloc(&m->d_Bop, sizeof(uint16_t) * bop.size()));
   CUDA_TRY(cudaMalloc(&m->d_mats, sizeof(TcMaterial) * mats.size()));
-  CUDA_TRY(cudaMalloc(&m->d_or, sizeof(unsigned long long) * 3));
+  const size_t or_words = 3 * (1 + (size_t)m->tiles_x * m->tiles_y);
+  CUDA_TRY(cudaMalloc(&m->d_or, sizeof(unsigned long long) * or_words));
   CUDA_TRY(cudaMalloc(&m->d_tcparams, sizeof(TcStepParams)));
   CUDA_TRY(cudaMalloc(&m->d_tcpersist, sizeof(int64_t) * 8));
   CUDA_TRY(cudaMalloc(&m->d_segs, sizeof(int4) * m->segs.size()));
@@ -591,7 +594,7 @@ static int build_tc(vfe_mesh *m) {
                       cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(m->d_mats, mats.data(), sizeof(TcMaterial) * mats.size(),
                       cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemset(m->d_or, 0, sizeof(unsigned long long) * 3));
+  CUDA_TRY(cudaMemset(m->d_or, 0, sizeof(unsigned long long) * or_words));
   int64_t persist[8] = {0, 0, 0, 0, (int64_t)(m->eC + m->e_ref), 0, 0, 0};
   CUDA_TRY(cudaMemcpy(m->d_tcpersist, persist, sizeof(persist), cudaMemcpyHostToDevice));
   // TMA maps over the two state buffers: (x, y, z, component), int64, box 18x17x1x3
@@ -863,10 +866,24 @@ int vfe_set_state(vfe_mesh *m, const double *u, const double *u_prev) {
                         cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(m->d_U[1 - m->cur], U1.data(), sizeof(int64_t) * U1.size(),
                         cudaMemcpyHostToDevice));
-    // the next prologue reads slot (step + 2) % 3 for the bit length of u^n
-    unsigned long long slots[3] = {0, 0, 0};
-    slots[(m->steps + 2) % 3] = o0 | o1;
-    CUDA_TRY(cudaMemcpy(m->d_or, slots, sizeof(slots), cudaMemcpyHostToDevice));
+    // the next step reads slot (step + 2) % 3: the global bound of |u^n|,
+    // |u^{n-1}| and one bound per 15x15 node column (its digit quantum)
+    const int ncols = m->tiles_x * m->tiles_y;
+    std::vector<unsigned long long> slots(3 * (size_t)(1 + ncols), 0);
+    unsigned long long *sl = slots.data() + (size_t)((m->steps + 2) % 3) * (1 + ncols);
+    sl[0] = o0 | o1;
+    for (int64_t n = 0; n < m->nn; ++n) {
+      const int64_t i = n % (m->nx + 1), j = (n / (m->nx + 1)) % (m->ny + 1);
+      const int64_t t = tc_index(m, n);
+      unsigned long long o = 0;
+      for (int c = 0; c < 3; ++c) {
+        const int64_t a = U0[c * m->comp + t], b = U1[c * m->comp + t];
+        o |= (unsigned long long)(a < 0 ? -a : a) | (unsigned long long)(b < 0 ? -b : b);
+      }
+      sl[1 + (j / TC_OWN) * m->tiles_x + (i / TC_OWN)] |= o;
+    }
+    CUDA_TRY(cudaMemcpy(m->d_or, slots.data(), sizeof(unsigned long long) * slots.size(),
+                        cudaMemcpyHostToDevice));
     int64_t F64 = F, zero = 0;
     CUDA_TRY(cudaMemcpy(m->d_tcpersist, &F64, sizeof(int64_t), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(m->d_tcpersist + 5, &zero, sizeof(int64_t), cudaMemcpyHostToDevice));

@@ -24,7 +24,8 @@
 #define TC_THREADS 512          // two threads per element: corner groups dz = 0 / 1
 #define TC_MAX_MAT 64            // materials per mesh on the TC path
 #define TC_MAX_REC_CTA 64        // receivers handled per CTA work item
-#define TC_UNITS_BITS 56         // target bit length of max |U| after rescale
+#define TC_UNITS_BITS 59         // target bit length of max |U| after rescale
+                                 // (a step's growth keeps |U| below 2^62)
 
 // fp32 magic bias: 8 padding K-rows carry A = 128, B = 12288 so that every
 // accumulator starts from 1.5 * 2^23; its bit pattern is then 0x4B400000 + d
@@ -44,6 +45,8 @@ struct TcStepParams {     // written by the per-step prologue kernel
   int or_slot;            // slot this step ORs |U_new| into
   int rs_prev;            // shift of the previous step: u^{n-1} is stored in
                           // units 2^-(F_old + rs_prev)
+  int eCref;              // eC + e_ref (exponent bookkeeping for R)
+  int pad;
 };
 
 struct TcMaterial {       // per-material integer multipliers, mesh-wide unit
@@ -78,7 +81,9 @@ struct TcDevice {         // everything the TC kernels read (by value)
   const int32_t *recv_off;// segment -> first receiver, size n_segs+1
   int64_t src_node;       // -1: none
   double *traces;         // [rows][n_rec][3]
-  unsigned long long *or_slots;  // 3 slots of OR(|U_new|)
+  unsigned long long *or_slots;  // 3 slots x (1 + tiles_x*tiles_y): OR(|U|), global
+                                 // then per 15x15 node column
+  int tiles_x, tiles_y;
   int *status;            // device error flags (bit 0: wait timeout)
   const TcStepParams *params;
   int64_t *S_out;         // K u mode: per-node S (int64 x 3, SoA like U)
@@ -138,8 +143,8 @@ int tc_smem_bytes();
 cudaError_t tc_prepare();
 cudaError_t f64_prepare();
 cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t *persist,
-                                  const TcSource &src, unsigned long long *or_slots, int have_src,
-                                  int trace_on, int *status);
+                                  const TcSource &src, unsigned long long *or_slots, int ncols,
+                                  int have_src, int trace_on, int *status);
 cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
 
 size_t f64_params_bytes();

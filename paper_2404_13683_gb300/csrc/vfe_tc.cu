@@ -162,6 +162,23 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t &a, uint32_t &
                : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -376,10 +393,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     };
     // digitise node plane p into digit slot p mod 3: one task per (row,
     // x-chunk, component, stage) writes the dx = 0 and dx = 1 lines.  With the
-    // offset-binary bias boff = sum_s 1024 2^(11 s), digit s of floor(U/2^shq)
-    // is ((U + boff 2^shq) >> (shq + 11 s)) & 2047 - 1024 (nested floors);
-    // U + boff 2^shq is positive and below 2^63 because |U| < 2^(51+shq) and
-    // shq <= 8 (|U| < 2^59).
+    // offset-binary bias boff = sum_s 1024 2^(11 s), digit s of q = floor(U/2^shq)
+    // is ((q + boff) >> 11 s) & 2047 - 1024; q + boff is positive and below
+    // 2^55 because |q| < 2^51.
     constexpr int ntask = TC_NODES * 6 * STAGES;
     const int dtask = tid < ntask ? tid : -1;
     const int ds_ = s_lo + (dtask < 0 ? 0 : dtask / (TC_NODES * 6));
@@ -387,9 +403,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int dnj = dr_ / 6, dxc = (dr_ % 6) / 3, dc = dr_ % 3;
     const int dsrc = (dc * TC_NODES + dnj) * TC_BOXX + 8 * dxc + xo;
     const int ddst = ds_ * kStageBytes + (dnj * 2 + dxc) * kBlockBytes + dc * 16;
-    const uint64_t dbias = (uint64_t)((1LL << 10) | (1LL << 21) | (1LL << 32) | (1LL << 43) |
-                                      (1LL << 54)) << P.shq;
-    const int dshift = P.shq + TC_DIGIT_BITS * ds_;
+    // digit quantum of this segment (Eq. intscaling, per node column): the
+    // step uses the max |u| over the 3x3 node columns around the segment's
+    // column (its elements' nodes) from the previous step, never more than the
+    // global shift; K u and the diagnostic modes use the global shift
+    int shq = P.shq;
+    if (MODE == TC_MODE_STEP) {
+      const unsigned long long *prev =
+          d.or_slots + (size_t)((P.or_slot + 2) % 3) * (1 + d.tiles_x * d.tiles_y) + 1;
+      unsigned long long o = 0;
+      for (int dyc = -1; dyc <= 1; ++dyc)
+        for (int dxc = -1; dxc <= 1; ++dxc) {
+          const int cx = seg.x + dxc, cy = seg.y + dyc;
+          if (cx >= 0 && cy >= 0 && cx < d.tiles_x && cy < d.tiles_y) o |= prev[cy * d.tiles_x + cx];
+        }
+      const int b = o ? 64 - __clzll((long long)o) : 0;
+      shq = min(P.shq, max(0, b - TC_QBITS));
+    }
+    // S of this segment is in units 2^(63 - e_ref + shq) of the raw state
+    const int Rseg = P.eCref + P.rs - shq - 63;
+    const int64_t dbias = (1LL << 10) | (1LL << 21) | (1LL << 32) | (1LL << 43) | (1LL << 54);
+    const int dshift = TC_DIGIT_BITS * ds_;
+    unsigned long long or_seg = 0;
     auto digitise = [&](int p) {
       if (dtask < 0) return;
       const int64_t *src = uslot + (p & 3) * (kUSlotStride / 8) + dsrc;
@@ -398,7 +433,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       float f[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        const uint64_t v = (uint64_t)src[i] + dbias;
+        const uint64_t v = (uint64_t)((src[i] >> shq) + dbias);
         f[i] = int_to_f32_exact((int)((uint32_t)(v >> dshift) & 2047u) - 1024);
       }
       uint4 lo, hi;  // dx = 0 line: nodes 0..7, dx = 1 line: nodes 1..8
@@ -416,25 +451,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     };
     // one thread issues the MMAs of element layer L (node planes L, L+1),
     // tile 0 first, with one commit per tile
+    // A (MN-major): 8-element chunks at 128 B, K groups (dy) at 256 B; B (K-major):
+    // 8-row N groups at 128 B, K groups at 6*128 B.  Descriptors differ only in
+    // the start-address field (address >> 4, below 2^14 for shared memory), so
+    // they are formed by adding offsets to one base descriptor.
+    const uint64_t adesc0 = make_sdesc(smem_u32(digits), 2 * kBlockBytes, kBlockBytes);
+    const uint64_t bdesc0 = make_sdesc(smem_u32(bop), 6 * kBlockBytes, kBlockBytes);
     auto issue_mma = [&](int L) {
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t bbase = smem_u32(bop);
+        const int sl0 = ((L % kDigitSlots) + kDigitSlots) % kDigitSlots;
+        const int sl1 = sl0 == kDigitSlots - 1 ? 0 : sl0 + 1;
+        const uint64_t a0 = adesc0 + (uint64_t)((sl0 * kDigitSlotBytes) >> 4);
+        const uint64_t a1 = adesc0 + (uint64_t)((sl1 * kDigitSlotBytes) >> 4);
+#pragma unroll
         for (int t = 0; t < 2; ++t) {
+#pragma unroll
           for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
             const uint32_t dcol = tmem_base + (uint32_t)(t * kTileCols + s * TC_N);
-            for (int dz = 0; dz < 2; ++dz) {
-              const int p = L + dz;
-              const int slot = ((p % kDigitSlots) + kDigitSlots) % kDigitSlots;
-              const uint32_t abase = smem_u32(digits + slot * kDigitSlotBytes + s * kStageBytes +
-                                              (16 * t) * kBlockBytes);
-              // A (MN-major): 8-element chunks at 128 B, K groups (dy) at 256 B
-              const uint64_t adesc = make_sdesc(abase, 2 * kBlockBytes, kBlockBytes);
-              // B (K-major): 8-row N groups at 128 B, K groups at 6*128 B
-              const uint64_t bdesc = make_sdesc(bbase + dz * 2 * 6 * kBlockBytes, 6 * kBlockBytes,
-                                                kBlockBytes);
-              mma_f16(dcol, adesc, bdesc, dz);
-            }
+            const uint64_t off = (uint64_t)((s * kStageBytes + 16 * t * kBlockBytes) >> 4);
+            mma_f16(dcol, a0 + off, bdesc0, 0);
+            mma_f16(dcol, a1 + off, bdesc0 + (uint64_t)((2 * 6 * kBlockBytes) >> 4), 1);
           }
           mma_commit(&bars[4 + t]);
         }
@@ -492,7 +529,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int gg = 0; gg < 2; ++gg) {
         const int g = 2 * half + gg;
+        // this group's 12 outputs (dx, part, component) are 12 contiguous
+        // columns per stage; load all stages (x8 + x4 each), wait once
         uint32_t w[TC_MAX_STAGES][12];
+        const int c0 = 24 * half + 12 * gg;  // 0, 12, 24, 36
 #pragma unroll
         for (int s = 0; s < TC_MAX_STAGES; ++s) {
           if constexpr (s_lo > 0) {
@@ -502,10 +542,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               continue;
             }
           }
-          const uint32_t ta = tbase + (uint32_t)(s * TC_N + 12 * g);
-          tmem_ld4(ta + 0, w[s][0], w[s][1], w[s][2], w[s][3]);
-          tmem_ld4(ta + 4, w[s][4], w[s][5], w[s][6], w[s][7]);
-          tmem_ld4(ta + 8, w[s][8], w[s][9], w[s][10], w[s][11]);
+          const uint32_t ta = tbase + (uint32_t)(s * TC_N + c0);
+          if (gg == 0) {  // c0 = 0 or 24: x8 at c0, x4 at c0 + 8 (each aligned to its size)
+            tmem_ld8(ta, w[s]);
+            tmem_ld4(ta + 8, w[s][8], w[s][9], w[s][10], w[s][11]);
+          } else {        // c0 = 12 or 36: x4 at c0, x8 at c0 + 4
+            tmem_ld4(ta, w[s][0], w[s][1], w[s][2], w[s][3]);
+            tmem_ld8(ta + 4, w[s] + 4);
+          }
         }
         tmem_wait_ld();
         int64_t pq[12];
@@ -592,11 +636,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int64_t um = shr_round(uprev[c], P.rs + P.rs_prev);
             const __int128 prod = (__int128)S[c] * (__int128)cn;
             int64_t du;
-            if (P.R > 0) {
-              const int R = min(P.R, 126);
+            if (Rseg > 0) {
+              const int R = min(Rseg, 126);
               du = (int64_t)((prod + ((__int128)1 << (R - 1))) >> R);
             } else {  // the state is being scaled up: exact left shift
-              du = (int64_t)(prod << min(-P.R, 63));
+              du = (int64_t)(prod << min(-Rseg, 63));
             }
             int64_t un = 2 * u0 - um - du;
             if (is_src) un += P.dU_src[c];
@@ -604,7 +648,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             unew[c] = un;
             d.U_next[c * d.comp + nidx] = un;
             // the slot bounds u^{n+1} and u^n (both in the new units)
-            or_acc |= (unsigned long long)(un < 0 ? -un : un) |
+            or_seg |= (unsigned long long)(un < 0 ? -un : un) |
                       (unsigned long long)(u0 < 0 ? -u0 : u0);
           }
           for (int r = 0; r < nrec; ++r) {
@@ -618,14 +662,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
     }
+    if (MODE == TC_MODE_STEP) {  // per-column and global bounds for the next step
+      for (int o = 16; o > 0; o >>= 1) or_seg |= __shfl_xor_sync(0xffffffffu, or_seg, o);
+      if (lane == 0 && or_seg) {
+        unsigned long long *cur = d.or_slots + (size_t)P.or_slot * (1 + d.tiles_x * d.tiles_y);
+        atomicOr(&cur[1 + seg.y * d.tiles_x + seg.x], or_seg);
+        or_acc |= or_seg;
+      }
+    }
     __syncthreads();  // srecv and the U slots are reused by the next segment
   }
 
   // ---- teardown -------------------------------------------------------------
-  if (MODE == TC_MODE_STEP) {
-    for (int o = 16; o > 0; o >>= 1) or_acc |= __shfl_xor_sync(0xffffffffu, or_acc, o);
-    if (lane == 0 && or_acc) atomicOr(&d.or_slots[P.or_slot], or_acc);
-  }
+  if (MODE == TC_MODE_STEP && lane == 0 && or_acc)
+    atomicOr(&d.or_slots[(size_t)P.or_slot * (1 + d.tiles_x * d.tiles_y)], or_acc);
   if (aborted && tid == 0) atomicOr(d.status, 1);
   tc_fence_before();
   __syncthreads();
@@ -642,12 +692,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // persist[0] = F of u^n, [1] = step, [2] = trace rows, [4] = eC + e_ref,
 // [5] = shift of the last step (u^{n-1} has F + [5])
 __global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist, TcSource src_desc,
-                                   unsigned long long *or_slots, int have_src, int trace_on,
-                                   int *status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+                                   unsigned long long *or_slots, int ncols, int have_src,
+                                   int trace_on, int *status) {
   const int64_t n = persist[1];
+  // clear the slot (global + per column) that the next step will OR into
+  unsigned long long *next = or_slots + (size_t)((n + 1) % 3) * (1 + ncols);
+  for (int i = threadIdx.x; i < 1 + ncols; i += blockDim.x) next[i] = 0;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int F_old = (int)persist[0];
-  const unsigned long long orp = or_slots[(n + 2) % 3];
+  const unsigned long long orp = or_slots[(size_t)((n + 2) % 3) * (1 + ncols)];
   // bit lengths of max|u^n|, max|u^{n-1}| (raw units) and of the source
   // increment at the old scale; 'valid' flags separate zero from tiny
   const int b = orp ? 64 - __clzll((long long)orp) : 0;
@@ -687,9 +740,10 @@ __global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist, TcSou
   p.F = F_new;
   p.or_slot = (int)(n % 3);
   p.rs_prev = (int)persist[5];
+  p.eCref = (int)persist[4];
+  p.pad = 0;
   if (F_new < -2000 || F_new > 2000) atomicOr(status, 2);
   *params = p;
-  or_slots[(n + 1) % 3] = 0;
   persist[0] = F_new;
   persist[5] = rs;
   persist[1] = n + 1;
@@ -699,9 +753,10 @@ __global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist, TcSou
 int tc_smem_bytes() { return kSmemBytes; }
 
 cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t *persist,
-                                  const TcSource &src, unsigned long long *or_slots, int have_src,
-                                  int trace_on, int *status) {
-  tc_prologue_kernel<<<1, 32, 0, s>>>(params, persist, src, or_slots, have_src, trace_on, status);
+                                  const TcSource &src, unsigned long long *or_slots, int ncols,
+                                  int have_src, int trace_on, int *status) {
+  tc_prologue_kernel<<<1, 256, 0, s>>>(params, persist, src, or_slots, ncols, have_src, trace_on,
+                                       status);
   return cudaGetLastError();
 }
 
