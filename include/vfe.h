@@ -134,6 +134,23 @@ int vfe_debug_tc_partials(vfe_mesh *mesh, const double *u, int n,
                           const int64_t *ids, int64_t *out, int *shift_out,
                           int *frac_bits_out);
 
+/* Batches: many meshes advanced together (the paper's many-case use, Section 1).
+ * vfe_create_batch takes n distinct meshes on the tensor-core path, on one
+ * device and with the same digit stage count; it keeps pointers to them (they
+ * must outlive the batch).  vfe_batch_step(b, n) advances every mesh n steps
+ * with one fused kernel launch per step over all meshes' node columns (plus
+ * one per-step prologue launch), replayed as a captured CUDA graph; each mesh
+ * keeps its own source, receivers, traces, state and time step.  Work queued
+ * on a mesh's own stream before the call runs first; calls on a mesh after it
+ * wait for the batch.  Changing a mesh's source or receivers between batch
+ * steps is allowed (the batch rebuilds its tables).  vfe_batch_synchronize
+ * waits and reports device-side errors of every mesh. */
+typedef struct vfe_batch vfe_batch;
+int vfe_create_batch(int n, vfe_mesh *const *meshes, vfe_batch **out);
+int vfe_batch_step(vfe_batch *batch, int n);
+int vfe_batch_synchronize(vfe_batch *batch);
+int vfe_destroy_batch(vfe_batch *batch);
+
 /* K u of the tensor-core path for callers that cannot allocate device memory:
  * u and f are FP64 [nodes][3] host arrays as in vfe_internal_force, and the
  * result agrees with it to the same FP64-level tolerance.  The paper has no

@@ -176,9 +176,11 @@ struct vfe_mesh {
 
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_valid[2] = {false, false};
+  int64_t gen = 0;  // bumped whenever kernel arguments change (batches rebuild)
 };
 
 static void invalidate_graphs(vfe_mesh *m) {
+  m->gen++;
   for (int i = 0; i < 2; ++i) {
     if (m->graph[i]) cudaGraphExecDestroy(m->graph[i]);
     m->graph[i] = nullptr;
@@ -1091,6 +1093,306 @@ int vfe_debug_tc_partials(vfe_mesh *m, const double *u, int n, const int64_t *id
   for (int q = 0; q < n; ++q) memcpy(out + 48 * q, all.data() + 48 * ids[q], 48 * sizeof(int64_t));
   if (shift_out) *shift_out = shq;
   if (frac_bits_out) *frac_bits_out = F;
+  return VFE_OK;
+}
+
+}  // extern "C"
+
+// ---- batches: many meshes advanced by one launch per step -------------------
+
+struct vfe_batch {
+  std::vector<vfe_mesh *> meshes;
+  std::vector<int64_t> gens;
+  std::vector<int> base_cur;
+  int device = 0, stages = 0, sms = 1;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  int64_t steps = 0;  // steps taken since the arrays were built
+  std::vector<int4> segs;
+  std::vector<int32_t> seg_mesh, seg_off;
+  int4 *d_segs = nullptr;
+  int32_t *d_seg_mesh = nullptr, *d_seg_off = nullptr, *d_recv_off = nullptr;
+  TcRecv *d_recv = nullptr;
+  TcDevice *d_devs[2] = {nullptr, nullptr};
+  CUtensorMap *d_maps[2] = {nullptr, nullptr};
+  TcPrologueArgs *d_pro = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+static void batch_free_arrays(vfe_batch *b) {
+  void *ptrs[] = {b->d_segs, b->d_seg_mesh, b->d_seg_off, b->d_recv_off, b->d_recv,
+                  b->d_devs[0], b->d_devs[1], b->d_maps[0], b->d_maps[1], b->d_pro};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  b->d_segs = nullptr; b->d_seg_mesh = nullptr; b->d_seg_off = nullptr; b->d_recv_off = nullptr;
+  b->d_recv = nullptr; b->d_devs[0] = b->d_devs[1] = nullptr; b->d_maps[0] = b->d_maps[1] = nullptr;
+  b->d_pro = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    b->graph[i] = nullptr;
+  }
+}
+
+// (Re)build the partition, receivers and per-mesh argument arrays.
+static int batch_build(vfe_batch *b) {
+  batch_free_arrays(b);
+  const int nm = (int)b->meshes.size();
+  // column-planes of all meshes in order, split into one equal range per SM
+  std::vector<int64_t> start(nm + 1, 0);
+  for (int i = 0; i < nm; ++i) {
+    const vfe_mesh *m = b->meshes[i];
+    start[i + 1] = start[i] + (int64_t)m->tiles_x * m->tiles_y * (m->nz + 1);
+  }
+  const int64_t total = start[nm];
+  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(b->sms, total));
+  b->segs.clear();
+  b->seg_mesh.clear();
+  b->seg_off.assign(G + 1, 0);
+  for (int64_t g = 0; g < G; ++g) {
+    b->seg_off[g] = (int32_t)b->segs.size();
+    int64_t lo = g * total / G;
+    const int64_t hi = (g + 1) * total / G;
+    while (lo < hi) {
+      int mi = (int)(std::upper_bound(start.begin(), start.end(), lo) - start.begin()) - 1;
+      const vfe_mesh *m = b->meshes[mi];
+      const int64_t planes = m->nz + 1, loc = lo - start[mi];
+      const int64_t col = loc / planes, z0 = loc % planes;
+      const int64_t z1 = std::min<int64_t>(planes, z0 + std::min(hi, start[mi + 1]) - lo);
+      b->segs.push_back(make_int4((int)(col % m->tiles_x), (int)(col / m->tiles_x), (int)z0,
+                                  (int)z1));
+      b->seg_mesh.push_back(mi);
+      lo += z1 - z0;
+    }
+  }
+  b->seg_off[G] = (int32_t)b->segs.size();
+  // receivers per batch segment (indices into each mesh's own trace rows)
+  const int ns = (int)b->segs.size();
+  std::vector<std::vector<TcRecv>> per(ns);
+  for (int sg = 0; sg < ns; ++sg) {
+    const vfe_mesh *m = b->meshes[b->seg_mesh[sg]];
+    const int4 q = b->segs[sg];
+    for (int r = 0; r < m->n_rec; ++r) {
+      const int i = m->rec_ijk[3 * r], j = m->rec_ijk[3 * r + 1], k = m->rec_ijk[3 * r + 2];
+      if (i / TC_OWN == q.x && j / TC_OWN == q.y && k >= q.z && k < q.w) {
+        TcRecv v;
+        v.ei = (int16_t)(i - TC_OWN * q.x);
+        v.ej = (int16_t)(j - TC_OWN * q.y);
+        v.k = k;
+        v.r = r;
+        v.pad = 0;
+        per[sg].push_back(v);
+      }
+    }
+    if ((int)per[sg].size() > TC_MAX_REC_CTA)
+      return fail(VFE_EINVAL, "more than %d receivers in one node column segment", TC_MAX_REC_CTA);
+  }
+  std::vector<TcRecv> flat;
+  std::vector<int32_t> roff(ns + 1, 0);
+  for (int sg = 0; sg < ns; ++sg) {
+    roff[sg] = (int32_t)flat.size();
+    flat.insert(flat.end(), per[sg].begin(), per[sg].end());
+  }
+  roff[ns] = (int32_t)flat.size();
+  // kernel arguments of each mesh for both buffer parities, and prologue args
+  std::vector<TcDevice> devs[2];
+  std::vector<CUtensorMap> maps[2];
+  std::vector<TcPrologueArgs> pro(nm);
+  b->gens.resize(nm);
+  b->base_cur.resize(nm);
+  for (int i = 0; i < nm; ++i) {
+    vfe_mesh *m = b->meshes[i];
+    b->gens[i] = m->gen;
+    b->base_cur[i] = m->cur;
+    for (int p = 0; p < 2; ++p) {
+      const int cur = m->cur ^ p;
+      devs[p].push_back(tc_device(m, cur));
+      maps[p].push_back(m->tmap[cur]);
+    }
+    TcPrologueArgs &A = pro[i];
+    memset(&A, 0, sizeof(A));
+    A.params = m->d_tcparams;
+    A.persist = m->d_tcpersist;
+    A.or_slots = m->d_or;
+    A.status = m->d_status;
+    A.amp_scale = m->amp * m->src_scale;
+    A.dt = m->dt;
+    A.f0 = m->f0;
+    A.t0 = m->t0;
+    for (int c = 0; c < 3; ++c) A.dir[c] = m->src_dir[c];
+    A.ncols = m->tiles_x * m->tiles_y;
+    A.have_src = m->has_src ? 1 : 0;
+    A.trace_on = m->n_rec > 0 ? 1 : 0;
+  }
+  CUDA_TRY(cudaMalloc(&b->d_segs, sizeof(int4) * ns));
+  CUDA_TRY(cudaMalloc(&b->d_seg_mesh, sizeof(int32_t) * ns));
+  CUDA_TRY(cudaMalloc(&b->d_seg_off, sizeof(int32_t) * b->seg_off.size()));
+  CUDA_TRY(cudaMalloc(&b->d_recv, sizeof(TcRecv) * std::max<size_t>(flat.size(), 1)));
+  CUDA_TRY(cudaMalloc(&b->d_recv_off, sizeof(int32_t) * roff.size()));
+  CUDA_TRY(cudaMalloc(&b->d_pro, sizeof(TcPrologueArgs) * nm));
+  CUDA_TRY(cudaMemcpy(b->d_segs, b->segs.data(), sizeof(int4) * ns, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_seg_mesh, b->seg_mesh.data(), sizeof(int32_t) * ns,
+                      cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_seg_off, b->seg_off.data(), sizeof(int32_t) * b->seg_off.size(),
+                      cudaMemcpyHostToDevice));
+  if (!flat.empty())
+    CUDA_TRY(cudaMemcpy(b->d_recv, flat.data(), sizeof(TcRecv) * flat.size(),
+                        cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_recv_off, roff.data(), sizeof(int32_t) * roff.size(),
+                      cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(b->d_pro, pro.data(), sizeof(TcPrologueArgs) * nm, cudaMemcpyHostToDevice));
+  for (int p = 0; p < 2; ++p) {
+    CUDA_TRY(cudaMalloc(&b->d_devs[p], sizeof(TcDevice) * nm));
+    CUDA_TRY(cudaMalloc(&b->d_maps[p], sizeof(CUtensorMap) * nm));  // cudaMalloc: 256-B aligned
+    CUDA_TRY(cudaMemcpy(b->d_devs[p], devs[p].data(), sizeof(TcDevice) * nm,
+                        cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(b->d_maps[p], maps[p].data(), sizeof(CUtensorMap) * nm,
+                        cudaMemcpyHostToDevice));
+  }
+  b->steps = 0;
+  return VFE_OK;
+}
+
+static TcBatch batch_args(const vfe_batch *b, int parity) {
+  TcBatch a;
+  a.devs = b->d_devs[parity];
+  a.maps = b->d_maps[parity];
+  a.segs = b->d_segs;
+  a.seg_mesh = b->d_seg_mesh;
+  a.seg_off = b->d_seg_off;
+  a.recv = b->d_recv;
+  a.recv_off = b->d_recv_off;
+  a.n_ctas = (int)b->seg_off.size() - 1;
+  return a;
+}
+
+static int batch_enqueue(vfe_batch *b, int parity) {
+  CUDA_TRY(tc_launch_batch_prologue(b->stream, b->d_pro, (int)b->meshes.size()));
+  CUDA_TRY(tc_launch_batch_step(b->stream, batch_args(b, parity), b->stages));
+  return VFE_OK;
+}
+
+extern "C" {
+
+int vfe_create_batch(int n, vfe_mesh *const *meshes, vfe_batch **out) {
+  if (!out) return fail(VFE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !meshes) return fail(VFE_EINVAL, "need at least one mesh");
+  for (int i = 0; i < n; ++i) {
+    if (!meshes[i]) return fail(VFE_EINVAL, "mesh %d is NULL", i);
+    if (meshes[i]->opt.path != VFE_PATH_TC)
+      return fail(VFE_EINVAL, "mesh %d is not on the tensor-core path", i);
+    if (meshes[i]->device != meshes[0]->device)
+      return fail(VFE_EINVAL, "mesh %d is on another device", i);
+    if (meshes[i]->opt.stages != meshes[0]->opt.stages)
+      return fail(VFE_EINVAL, "mesh %d uses %d digit stages, mesh 0 uses %d", i,
+                  meshes[i]->opt.stages, meshes[0]->opt.stages);
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == meshes[i]) return fail(VFE_EINVAL, "mesh %d appears twice", i);
+  }
+  vfe_batch *b = new vfe_batch();
+  b->meshes.assign(meshes, meshes + n);
+  b->device = meshes[0]->device;
+  b->stages = meshes[0]->opt.stages;
+  b->sms = meshes[0]->sms;
+  int rc = VFE_OK;
+  cudaSetDevice(b->device);
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+    rc = fail(VFE_ECUDA, "batch stream/event creation failed");
+  } else {
+    for (vfe_mesh *m : b->meshes)
+      if (cudaStreamSynchronize(m->stream) != cudaSuccess) rc = fail(VFE_ECUDA, "mesh stream");
+    if (rc == VFE_OK) rc = batch_build(b);
+  }
+  if (rc != VFE_OK) {
+    std::string msg = g_last_error;
+    vfe_destroy_batch(b);
+    g_last_error = msg;
+    return rc;
+  }
+  *out = b;
+  return VFE_OK;
+}
+
+int vfe_destroy_batch(vfe_batch *b) {
+  if (!b) return VFE_OK;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_free_arrays(b);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return VFE_OK;
+}
+
+int vfe_batch_step(vfe_batch *b, int n) {
+  if (!b) return fail(VFE_EINVAL, "batch is NULL");
+  if (n < 0) return fail(VFE_EINVAL, "n must be >= 0");
+  if (n == 0) return VFE_OK;
+  cudaSetDevice(b->device);
+  // earlier work queued on the meshes' own streams comes first
+  for (vfe_mesh *m : b->meshes) {
+    CUDA_TRY(cudaEventRecord(b->done, m->stream));
+    CUDA_TRY(cudaStreamWaitEvent(b->stream, b->done, 0));
+  }
+  bool rebuild = false;
+  for (size_t i = 0; i < b->meshes.size(); ++i) {
+    vfe_mesh *m = b->meshes[i];
+    int rc = ensure_trace_capacity(m, m->trace_rows + n);
+    if (rc != VFE_OK) return rc;
+    if (m->gen != b->gens[i] || m->cur != (b->base_cur[i] ^ (int)(b->steps & 1))) rebuild = true;
+  }
+  if (rebuild) {
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    int rc = batch_build(b);
+    if (rc != VFE_OK) return rc;
+  }
+  int64_t left = n;
+  while (left >= 2) {
+    const int parity = (int)(b->steps & 1);
+    if (!b->graph[parity]) {
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      int rc = batch_enqueue(b, parity);
+      if (rc == VFE_OK) rc = batch_enqueue(b, 1 - parity);
+      cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+      if (rc != VFE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return fail(VFE_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(VFE_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    }
+    CUDA_TRY(cudaGraphLaunch(b->graph[parity], b->stream));
+    b->steps += 2;
+    left -= 2;
+  }
+  if (left == 1) {
+    int rc = batch_enqueue(b, (int)(b->steps & 1));
+    if (rc != VFE_OK) return rc;
+    b->steps += 1;
+  }
+  for (vfe_mesh *m : b->meshes) {
+    if (n & 1) m->cur = 1 - m->cur;
+    m->steps += n;
+    if (m->n_rec) m->trace_rows += n;
+  }
+  // later work on the meshes' own streams (traces, state) waits for the batch
+  CUDA_TRY(cudaEventRecord(b->done, b->stream));
+  for (vfe_mesh *m : b->meshes) CUDA_TRY(cudaStreamWaitEvent(m->stream, b->done, 0));
+  return VFE_OK;
+}
+
+int vfe_batch_synchronize(vfe_batch *b) {
+  if (!b) return fail(VFE_EINVAL, "batch is NULL");
+  cudaSetDevice(b->device);
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  for (vfe_mesh *m : b->meshes) {
+    int rc = check_status(m);
+    if (rc != VFE_OK) return rc;
+  }
   return VFE_OK;
 }
 

@@ -90,6 +90,29 @@ struct TcDevice {         // everything the TC kernels read (by value)
   int64_t *partials_out;  // partials mode: per element 48 int64 (element order)
 };
 
+// Several meshes advanced by one launch: each segment belongs to one mesh,
+// whose kernel arguments and tensor map live in global memory.
+struct TcBatch {
+  const TcDevice *devs;       // per mesh; nullptr for a single-mesh launch
+  const CUtensorMap *maps;    // per mesh (64-byte aligned)
+  const int4 *segs;           // (tile x, tile y, z0, z1) of every segment
+  const int32_t *seg_mesh;    // mesh of each segment
+  const int32_t *seg_off;     // CTA -> first segment, size n_ctas+1
+  const TcRecv *recv;         // receivers grouped per batch segment
+  const int32_t *recv_off;    // segment -> first receiver
+  int n_ctas;
+};
+
+struct TcPrologueArgs {       // one mesh's inputs to the per-step prologue
+  TcStepParams *params;
+  int64_t *persist;
+  unsigned long long *or_slots;
+  int *status;
+  double amp_scale, dt, f0, t0;
+  double dir[3];
+  int ncols, have_src, trace_on, pad;
+};
+
 // FP64 path ------------------------------------------------------------------
 #define F64_MAX_MAT 24    // element matrices kept in shared memory
 
@@ -146,6 +169,8 @@ cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t 
                                   const TcSource &src, unsigned long long *or_slots, int ncols,
                                   int have_src, int trace_on, int *status);
 cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
+cudaError_t tc_launch_batch_prologue(cudaStream_t s, const TcPrologueArgs *args, int n_meshes);
+cudaError_t tc_launch_batch_step(cudaStream_t s, const TcBatch &b, int stages);
 
 size_t f64_params_bytes();
 cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,

@@ -34,6 +34,8 @@
 // update their node.
 #include <cuda_fp16.h>
 
+#include <cstring>
+
 #include "vfe_internal.h"
 
 namespace {
@@ -59,7 +61,8 @@ constexpr int kOffYbuf = kOffBop + kBopBytes;
 constexpr int kOffCbuf = kOffYbuf + kYbufBytes;
 constexpr int kOffMat = kOffCbuf + kCbufBytes;
 constexpr int kOffRecv = kOffMat + TC_MAX_MAT * (int)sizeof(TcMaterial);
-constexpr int kOffBar = kOffRecv + TC_MAX_REC_CTA * (int)sizeof(TcRecv);
+constexpr int kOffDev = kOffRecv + TC_MAX_REC_CTA * (int)sizeof(TcRecv);
+constexpr int kOffBar = kOffDev + ((int)sizeof(TcDevice) + 15) / 16 * 16;
 constexpr int kOffMisc = kOffBar + 8 * 8;
 constexpr int kSmemUsed = kOffMisc + 64;
 // padded so that only one CTA fits per SM (it allocates 512 TMEM columns)
@@ -286,7 +289,8 @@ __device__ __forceinline__ int64_t mul2_hi63(int64_t P, int64_t Q, int A1, int A
 // ---------------------------------------------------------------------------
 template <int MODE, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_step_kernel(const __grid_constant__ CUtensorMap tmap_u, const TcDevice d) {
+    tc_step_kernel(const __grid_constant__ CUtensorMap tmap_u, const TcDevice d0,
+                   const TcBatch b) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *digits = smem + kOffDigits;
   int64_t *uslot = reinterpret_cast<int64_t *>(smem + kOffU);
@@ -295,12 +299,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   int64_t *cbuf = reinterpret_cast<int64_t *>(smem + kOffCbuf);
   TcMaterial *smat = reinterpret_cast<TcMaterial *>(smem + kOffMat);
   TcRecv *srecv = reinterpret_cast<TcRecv *>(smem + kOffRecv);
+  TcDevice *sdev = reinterpret_cast<TcDevice *>(smem + kOffDev);  // batch: current mesh
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..3: U slots, 4,5: MMA tiles
   uint32_t *misc = reinterpret_cast<uint32_t *>(smem + kOffMisc);  // [0] tmem base, [1] abort
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const TcStepParams P = *d.params;
+  const bool batched = b.devs != nullptr;
   // with fewer stages the low digits are dropped (the top ones carry the value)
   constexpr int s_lo = TC_MAX_STAGES - STAGES;
 
@@ -326,9 +331,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  const uint16_t *bop_src = batched ? b.devs[0].Bop : d0.Bop;  // the same for every mesh
   for (int i = tid; i < kBopBytes / 16; i += TC_THREADS)
-    reinterpret_cast<uint4 *>(bop)[i] = reinterpret_cast<const uint4 *>(d.Bop)[i];
-  for (int i = tid; i < d.n_mat; i += TC_THREADS) smat[i] = d.mats[i];
+    reinterpret_cast<uint4 *>(bop)[i] = reinterpret_cast<const uint4 *>(bop_src)[i];
+  if (!batched)
+    for (int i = tid; i < d0.n_mat; i += TC_THREADS) smat[i] = d0.mats[i];
   {  // magic rows (lines 6 and 7 of every block) of every digit slot and stage
     const uint32_t mg = (uint32_t)__half_as_ushort(__float2half(TC_MAGIC_A));
     const uint4 mv = make_uint4(mg | (mg << 16), mg | (mg << 16), mg | (mg << 16), mg | (mg << 16));
@@ -346,8 +353,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint32_t uphase = 0;   // parity bit per U slot
   uint32_t mma_phase = 0;
   bool aborted = false;
-  unsigned long long or_acc = 0;
   const TcMaterial zero_mat = {0, 0, 0, 0};
+  int cur_mesh = -1;
 
   auto sync_abort = [&](bool ok) -> bool {  // true if the CTA must stop
     if (!ok) atomicExch(&misc[1], 1u);
@@ -355,9 +362,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     return misc[1] != 0;
   };
 
-  const int sbeg = d.seg_off[blockIdx.x], send = d.seg_off[blockIdx.x + 1];
+  const int sbeg = batched ? b.seg_off[blockIdx.x] : d0.seg_off[blockIdx.x];
+  const int send = batched ? b.seg_off[blockIdx.x + 1] : d0.seg_off[blockIdx.x + 1];
   for (int sg = sbeg; sg < send && !aborted; ++sg) {
-    const int4 seg = d.segs[sg];
+    // the mesh of this segment: arguments and materials in shared memory
+    if (batched) {
+      const int mesh = b.seg_mesh[sg];
+      if (mesh != cur_mesh) {
+        __syncthreads();  // the previous mesh's copies are no longer read
+        if (tid == 0) *sdev = b.devs[mesh];
+        __syncthreads();
+        for (int i = tid; i < sdev->n_mat; i += TC_THREADS) smat[i] = sdev->mats[i];
+        __syncthreads();
+        cur_mesh = mesh;
+      }
+    }
+    const TcDevice &d = batched ? *sdev : d0;
+    const CUtensorMap *tmap = batched ? &b.maps[cur_mesh] : &tmap_u;
+    const TcStepParams P = *d.params;
+    const int4 seg = batched ? b.segs[sg] : d.segs[sg];
     const int X0 = TC_OWN * seg.x - 1;  // global x of local element/node column 0
     const int Y0 = TC_OWN * seg.y - 1;
     const int Z0 = seg.z, Z1 = seg.w;   // owned node planes [Z0, Z1)
@@ -373,16 +396,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // the barriers of its last layer)
     int nrec = 0;
     if (MODE == TC_MODE_STEP && d.n_rec > 0 && P.trace_row >= 0) {
-      const int rbeg = d.recv_off[sg];
-      nrec = min(d.recv_off[sg + 1] - rbeg, TC_MAX_REC_CTA);
-      for (int i = tid; i < nrec; i += TC_THREADS) srecv[i] = d.recv[rbeg + i];
+      const int32_t *roff = batched ? b.recv_off : d.recv_off;
+      const TcRecv *rv = batched ? b.recv : d.recv;
+      const int rbeg = roff[sg];
+      nrec = min(roff[sg + 1] - rbeg, TC_MAX_REC_CTA);
+      for (int i = tid; i < nrec; i += TC_THREADS) srecv[i] = rv[rbeg + i];
     }
 
     auto issue_plane = [&](int p) {  // TMA of node plane p into U slot p & 3
       if (tid == 0) {
         const int s = p & 3;
         mbar_expect_tx(&bars[s], kUSlotBytes);
-        tma_load_u(uslot + s * (kUSlotStride / 8), &tmap_u, &bars[s], xbox, Y0, p);
+        tma_load_u(uslot + s * (kUSlotStride / 8), tmap, &bars[s], xbox, Y0, p);
       }
     };
     auto wait_plane = [&](int p) -> bool {
@@ -667,16 +692,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (lane == 0 && or_seg) {
         unsigned long long *cur = d.or_slots + (size_t)P.or_slot * (1 + d.tiles_x * d.tiles_y);
         atomicOr(&cur[1 + seg.y * d.tiles_x + seg.x], or_seg);
-        or_acc |= or_seg;
+        atomicOr(&cur[0], or_seg);
       }
     }
     __syncthreads();  // srecv and the U slots are reused by the next segment
   }
 
   // ---- teardown -------------------------------------------------------------
-  if (MODE == TC_MODE_STEP && lane == 0 && or_acc)
-    atomicOr(&d.or_slots[(size_t)P.or_slot * (1 + d.tiles_x * d.tiles_y)], or_acc);
-  if (aborted && tid == 0) atomicOr(d.status, 1);
+  if (aborted && tid == 0) atomicOr(batched ? b.devs[0].status : d0.status, 1);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -691,14 +714,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ---------------------------------------------------------------------------
 // persist[0] = F of u^n, [1] = step, [2] = trace rows, [4] = eC + e_ref,
 // [5] = shift of the last step (u^{n-1} has F + [5])
-__global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist, TcSource src_desc,
-                                   unsigned long long *or_slots, int ncols, int have_src,
-                                   int trace_on, int *status) {
+// One mesh's prologue, run by a block (thread 0 does the scalar work).
+__device__ void prologue_body(const TcPrologueArgs &A) {
+  int64_t *persist = A.persist;
+  unsigned long long *or_slots = A.or_slots;
+  const int ncols = A.ncols;
   const int64_t n = persist[1];
   // clear the slot (global + per column) that the next step will OR into
   unsigned long long *next = or_slots + (size_t)((n + 1) % 3) * (1 + ncols);
   for (int i = threadIdx.x; i < 1 + ncols; i += blockDim.x) next[i] = 0;
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (threadIdx.x != 0) return;
   const int F_old = (int)persist[0];
   const unsigned long long orp = or_slots[(size_t)((n + 2) % 3) * (1 + ncols)];
   // bit lengths of max|u^n|, max|u^{n-1}| (raw units) and of the source
@@ -707,14 +732,12 @@ __global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist, TcSou
   double src[3] = {0.0, 0.0, 0.0};
   int bs = 0;
   bool bs_valid = false;
-  if (have_src) {
+  if (A.have_src) {
     // F^n = amp ricker(n dt) dir, scaled by dt^2 / m of the source node
-    const double fv = src_desc.amp_scale * ricker_wavelet((double)n * src_desc.dt, src_desc.f0,
-                                                          src_desc.t0);
-    const double dir[3] = {src_desc.dir[0], src_desc.dir[1], src_desc.dir[2]};
+    const double fv = A.amp_scale * ricker_wavelet((double)n * A.dt, A.f0, A.t0);
     double mx = 0.0;
     for (int c = 0; c < 3; ++c) {
-      src[c] = fv * dir[c];
+      src[c] = fv * A.dir[c];
       mx = fmax(mx, fabs(src[c]));
     }
     if (mx > 0.0) {
@@ -732,8 +755,8 @@ __global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist, TcSou
   const int R = (int)persist[4] + rs - shq - 63;
   TcStepParams p;
   p.step = n;
-  p.trace_row = trace_on ? persist[2] : -1;
-  for (int c = 0; c < 3; ++c) p.dU_src[c] = have_src ? llrint(ldexp(src[c], F_new)) : 0;
+  p.trace_row = A.trace_on ? persist[2] : -1;
+  for (int c = 0; c < 3; ++c) p.dU_src[c] = A.have_src ? llrint(ldexp(src[c], F_new)) : 0;
   p.rs = rs;
   p.shq = shq;
   p.R = R;
@@ -742,12 +765,20 @@ __global__ void tc_prologue_kernel(TcStepParams *params, int64_t *persist, TcSou
   p.rs_prev = (int)persist[5];
   p.eCref = (int)persist[4];
   p.pad = 0;
-  if (F_new < -2000 || F_new > 2000) atomicOr(status, 2);
-  *params = p;
+  if (F_new < -2000 || F_new > 2000) atomicOr(A.status, 2);
+  *A.params = p;
   persist[0] = F_new;
   persist[5] = rs;
   persist[1] = n + 1;
-  if (trace_on) persist[2] += 1;
+  if (A.trace_on) persist[2] += 1;
+}
+
+// persist[0] = F of u^n, [1] = step, [2] = trace rows, [4] = eC + e_ref,
+// [5] = shift of the last step (u^{n-1} has F + [5])
+__global__ void tc_prologue_kernel(const TcPrologueArgs A) { prologue_body(A); }
+
+__global__ void tc_batch_prologue_kernel(const TcPrologueArgs *args) {
+  prologue_body(args[blockIdx.x]);
 }
 
 int tc_smem_bytes() { return kSmemBytes; }
@@ -755,8 +786,26 @@ int tc_smem_bytes() { return kSmemBytes; }
 cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t *persist,
                                   const TcSource &src, unsigned long long *or_slots, int ncols,
                                   int have_src, int trace_on, int *status) {
-  tc_prologue_kernel<<<1, 256, 0, s>>>(params, persist, src, or_slots, ncols, have_src, trace_on,
-                                       status);
+  TcPrologueArgs A;
+  A.params = params;
+  A.persist = persist;
+  A.or_slots = or_slots;
+  A.status = status;
+  A.amp_scale = src.amp_scale;
+  A.dt = src.dt;
+  A.f0 = src.f0;
+  A.t0 = src.t0;
+  for (int c = 0; c < 3; ++c) A.dir[c] = src.dir[c];
+  A.ncols = ncols;
+  A.have_src = have_src;
+  A.trace_on = trace_on;
+  A.pad = 0;
+  tc_prologue_kernel<<<1, 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_batch_prologue(cudaStream_t s, const TcPrologueArgs *args, int n_meshes) {
+  tc_batch_prologue_kernel<<<n_meshes, 256, 0, s>>>(args);
   return cudaGetLastError();
 }
 
@@ -784,22 +833,35 @@ cudaError_t tc_prepare() {
 }
 
 template <int MODE>
-static cudaError_t launch_mode(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap) {
-  const dim3 grid(d.n_ctas), block(TC_THREADS);
-  switch (d.stages) {
-    case 1: tc_step_kernel<MODE, 1><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
-    case 2: tc_step_kernel<MODE, 2><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
-    case 3: tc_step_kernel<MODE, 3><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
-    case 4: tc_step_kernel<MODE, 4><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
-    default: tc_step_kernel<MODE, 5><<<grid, block, kSmemBytes, s>>>(*tmap, d); break;
+static cudaError_t launch_mode(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap,
+                               const TcBatch &b, int stages, int n_ctas) {
+  const dim3 grid(n_ctas), block(TC_THREADS);
+  switch (stages) {
+    case 1: tc_step_kernel<MODE, 1><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    case 2: tc_step_kernel<MODE, 2><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    case 3: tc_step_kernel<MODE, 3><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    case 4: tc_step_kernel<MODE, 4><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    default: tc_step_kernel<MODE, 5><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode) {
+  TcBatch none;
+  memset(&none, 0, sizeof(none));
   switch (mode) {
-    case TC_MODE_STEP: return launch_mode<TC_MODE_STEP>(s, d, tmap);
-    case TC_MODE_KU: return launch_mode<TC_MODE_KU>(s, d, tmap);
-    default: return launch_mode<TC_MODE_PARTIALS>(s, d, tmap);
+    case TC_MODE_STEP: return launch_mode<TC_MODE_STEP>(s, d, tmap, none, d.stages, d.n_ctas);
+    case TC_MODE_KU: return launch_mode<TC_MODE_KU>(s, d, tmap, none, d.stages, d.n_ctas);
+    default: return launch_mode<TC_MODE_PARTIALS>(s, d, tmap, none, d.stages, d.n_ctas);
   }
+}
+
+// All meshes of a batch in one launch (the tensor-map and device-struct
+// arguments of the single-mesh form are unused placeholders here).
+cudaError_t tc_launch_batch_step(cudaStream_t s, const TcBatch &b, int stages) {
+  TcDevice none;
+  memset(&none, 0, sizeof(none));
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  return launch_mode<TC_MODE_STEP>(s, none, &dummy, b, stages, b.n_ctas);
 }

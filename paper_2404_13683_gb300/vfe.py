@@ -33,6 +33,7 @@ EXPORTS = (
     "vfe_get_traces", "vfe_get_dt", "vfe_get_sizes", "vfe_get_step_count",
     "vfe_get_state", "vfe_set_state", "vfe_last_error", "vfe_debug_tc_partials",
     "vfe_get_trace_rows", "vfe_internal_force_noalloc",
+    "vfe_create_batch", "vfe_batch_step", "vfe_batch_synchronize", "vfe_destroy_batch",
 )
 
 
@@ -76,6 +77,10 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_set_receivers.argtypes = [P, I, P]
     L.vfe_internal_force.argtypes = [P, P, P]
     L.vfe_internal_force_noalloc.argtypes = [P, P, P]
+    L.vfe_create_batch.argtypes = [I, P, ctypes.POINTER(ctypes.c_void_p)]
+    L.vfe_batch_step.argtypes = [P, I]
+    L.vfe_batch_synchronize.argtypes = [P]
+    L.vfe_destroy_batch.argtypes = [P]
     L.vfe_step.argtypes = [P, I]
     L.vfe_synchronize.argtypes = [P]
     L.vfe_get_traces.argtypes = [P, P, ctypes.POINTER(I64)]
@@ -229,6 +234,58 @@ def vfe_debug_tc_partials(mesh, u, element_ids):
     _check(load().vfe_debug_tc_partials(mesh, _p(u), len(ids), _p(ids), _p(out),
                                         ctypes.byref(sh), ctypes.byref(fb)))
     return out, sh.value, fb.value
+
+
+def vfe_create_batch(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                             for h in handles])
+    out = ctypes.c_void_p()
+    _check(load().vfe_create_batch(len(handles), ctypes.cast(arr, ctypes.c_void_p),
+                                   ctypes.byref(out)))
+    return out
+
+
+def vfe_batch_step(batch, n):
+    _check(load().vfe_batch_step(batch, int(n)))
+
+
+def vfe_batch_synchronize(batch):
+    _check(load().vfe_batch_synchronize(batch))
+
+
+def vfe_destroy_batch(batch):
+    _check(load().vfe_destroy_batch(batch))
+
+
+class Batch:
+    """Several ``Mesh`` objects advanced by one fused launch per step."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        self.handle = vfe_create_batch([m.handle for m in self.meshes])
+
+    def step(self, n):
+        vfe_batch_step(self.handle, n)
+
+    def synchronize(self):
+        vfe_batch_synchronize(self.handle)
+
+    def close(self):
+        if self.handle:
+            vfe_destroy_batch(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Mesh:

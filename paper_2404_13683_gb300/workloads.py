@@ -14,6 +14,9 @@ below stand in for it:
   2,000 steps, 64 receivers (the benchmark workload).
 * ``config3``: 512x512x256, ten dipping layers, seeded smoothed topography
   (cells above it are void), 5,000 steps.
+* ``config4``: 64 independent cubic models, n ~ U{32..128} (seeded), three
+  random layers each, random source node and frequency (3-10 Hz), 1,000
+  steps each -- the many-case batch.
 * ``random_mesh``: small random meshes with voids for parity tests.
 """
 from __future__ import annotations
@@ -111,6 +114,25 @@ def config3(seed: int = 3, shape=(512, 512, 256)):
                                       surface[max(j - 1, 0), max(i - 1, 0)]))))
     return _mesh((nx, ny, nz), 1.0, mat, table, _source(src, 5.0), rec, 5000,
                  "config3_%dx%dx%d" % (nx, ny, nz))
+
+
+def config4(seed: int = 4, n_models: int = 64, n_min: int = 32, n_max: int = 128):
+    """Many-case batch: independent cubic three-layer models of uneven sizes."""
+    rng = np.random.default_rng(seed)
+    models = []
+    for i in range(n_models):
+        n = int(rng.integers(n_min, n_max + 1))
+        vs = rng.uniform(200.0, 1000.0, size=3)
+        table = [[2.5 * v, v, float(rng.uniform(1700.0, 2300.0))] for v in vs]
+        b1, b2 = sorted(rng.integers(1, n, size=2))
+        k = np.arange(n)[:, None, None] * np.ones((n, n, n), dtype=np.int64)
+        mat = np.where(k >= b2, 0, np.where(k >= b1, 1, 2))
+        src = (int(rng.integers(1, n)), int(rng.integers(1, n)), int(rng.integers(1, n)))
+        rec = [(n // 4 + a * n // 2, n // 4 + b * n // 2, n) for b in range(2) for a in range(2)]
+        models.append(_mesh((n, n, n), 1.0, mat, table,
+                            _source(src, float(rng.uniform(3.0, 10.0))), rec, 1000,
+                            "config4_model%02d_%d" % (i, n)))
+    return models
 
 
 def random_mesh(seed: int, shape=None, n_mat: int = 3, void_frac: float = 0.1, h=None):
