@@ -134,6 +134,21 @@ int vfe_debug_tc_partials(vfe_mesh *mesh, const double *u, int n,
                           const int64_t *ids, int64_t *out, int *shift_out,
                           int *frac_bits_out);
 
+/* Adjoint-state gradient (the paper's internal-structure estimation use,
+ * Section 1).  For a run of nsteps from rest with the mesh's source and the
+ * receiver misfit J = 1/2 sum_{n<N} sum_r |u^{n+1}(r) - data[n][r]|^2
+ * (data: [nsteps][n_rec][3]), writes dJ/dG_e for every element (grad_G[ne],
+ * shear modulus G_e at fixed bulk modulus kappa_e; 0 for void cells) and J.
+ * The discrete adjoint of Eq. eqtimehistory is the same leapfrog run backward
+ * with the residual injected at the receivers; the forward states are
+ * recomputed from checkpoints taken every checkpoint_every steps (memory:
+ * checkpoint_every + 1 FP64 states plus two states per checkpoint), and
+ * dJ/dG_e = dt^2 sum_n mu^n_e . (dK_e/dG) u^n_e.  Uses the mesh's path for
+ * every step.  The mesh is left at rest (step 0, traces cleared).
+ * Synchronous. */
+int vfe_misfit_gradient(vfe_mesh *mesh, int nsteps, const double *data, int checkpoint_every,
+                        double *grad_G, double *misfit);
+
 /* Batches: many meshes advanced together (the paper's many-case use, Section 1).
  * vfe_create_batch takes n distinct meshes on the tensor-core path, on one
  * device and with the same digit stage count; it keeps pointers to them (they

@@ -58,6 +58,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_ricker.restype = d
         L.oracle_run.argtypes = [i, i, i, i, d, p, p, i, i, d, i, i64, p, d, d, d,
                                  i, p, p, p, p, p, p]
+        L.oracle_misfit_gradient.argtypes = [i, i, i, i, d, p, p, i, i, d, i, i64, p, d, d, d,
+                                             i, p, p, p, p]
         _lib = L
     return _lib
 
@@ -182,3 +184,25 @@ def run(kind, mesh, dt_, nsteps, source=None, receivers=(), fix_bottom=True,
     if return_state:
         return tr, uo, umo
     return tr
+
+
+def misfit_gradient(kind, mesh, dt_, nsteps, source, receivers, data, fix_bottom=True):
+    """(dJ/dG per element, J) of the receiver misfit against ``data``."""
+    mat, tab = _mesh_args(mesh)
+    nx, ny, nz = mesh["shape"]
+    rec = np.ascontiguousarray(receivers, dtype=np.int64).reshape(-1)
+    data = _f64(data).reshape(-1)
+    grad = np.zeros(nx * ny * nz)
+    J = ctypes.c_double()
+    if source is None:
+        src_node, sdir, f0, t0, amp = -1, np.zeros(3), 1.0, 0.0, 0.0
+    else:
+        src_node, sdir, f0, t0, amp = (int(source["node"]), _f64(source["dir"]),
+                                       float(source["f0"]), float(source["t0"]),
+                                       float(source["amp"]))
+    sdir = _f64(sdir)
+    _check(lib().oracle_misfit_gradient(kind, nx, ny, nz, mesh["h"], _ptr(mat), _ptr(tab), len(tab),
+                                        int(fix_bottom), dt_, nsteps, src_node, _ptr(sdir), f0, t0,
+                                        amp, len(rec), _ptr(rec), _ptr(data), _ptr(grad),
+                                        ctypes.byref(J)), "misfit_gradient")
+    return grad, J.value

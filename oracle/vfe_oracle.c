@@ -650,3 +650,101 @@ done:
   free(mass); free(u); free(up); free(un); free(f); free(fixed);
   return rc;
 }
+
+/* ---------- adjoint-state gradient (plain loops, all states stored) ------ */
+
+int oracle_misfit_gradient(int kind, int nx, int ny, int nz, double ds,
+                           const int32_t *mat, const double *table, int n_mat,
+                           int fix_bottom, double dt, int nsteps,
+                           int64_t src_node, const double *src_dir, double f0,
+                           double t0, double amp, int n_rec,
+                           const int64_t *rec_nodes, const double *data,
+                           double *grad, double *misfit) {
+  if (check_mesh(nx, ny, nz, mat, n_mat) || nsteps < 1 || n_rec < 1 || !data || !grad) return -1;
+  const int N = nsteps;
+  int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1), ne = (int64_t)nx * ny * nz;
+  size_t sz = 3 * (size_t)nn;
+  double *U = (double *)calloc(sz * (size_t)(N + 1), sizeof(double)); /* u^0 .. u^N */
+  double *tr = (double *)malloc(sizeof(double) * 3 * (size_t)n_rec * N);
+  double *mass = (double *)malloc(sizeof(double) * nn);
+  double *mu0 = (double *)calloc(sz, sizeof(double));  /* mu^{m+1} */
+  double *mu1 = (double *)calloc(sz, sizeof(double));  /* mu^m */
+  double *mu2 = (double *)calloc(sz, sizeof(double));  /* mu^{m-1} */
+  double *Kmu = (double *)malloc(sizeof(double) * sz);
+  double *g = (double *)malloc(sizeof(double) * sz);
+  double *Kg = (double *)malloc(sizeof(double) * 576 * n_mat);
+  char *fixed = (char *)malloc((size_t)nn);
+  int rc = -1;
+  if (!U || !tr || !mass || !mu0 || !mu1 || !mu2 || !Kmu || !g || !Kg || !fixed) goto done;
+  if (oracle_node_mass(kind, nx, ny, nz, ds, mat, table, n_mat, mass)) goto done;
+  for (int64_t n = 0; n < nn; ++n) {
+    int nk = (int)(n / ((int64_t)(nx + 1) * (ny + 1)));
+    fixed[n] = (char)((fix_bottom && nk == 0) || mass[n] == 0.0);
+  }
+  /* forward: the same run as oracle_run, keeping every state */
+  for (int it = 0; it < N; ++it) {
+    double *u = U + sz * it, *un = U + sz * (it + 1);
+    const double *up = it > 0 ? U + sz * (it - 1) : U;  /* u^{-1} = u^0 = 0 */
+    if (oracle_ku(kind, nx, ny, nz, ds, mat, table, n_mat, 0, u, Kmu)) goto done;
+    double fsrc = src_node >= 0 ? amp * oracle_ricker(it * dt, f0, t0) : 0.0;
+    for (int64_t n = 0; n < nn; ++n)
+      for (int c = 0; c < 3; ++c) {
+        int64_t d = 3 * n + c;
+        if (fixed[n]) { un[d] = 0.0; continue; }
+        double F = (n == src_node) ? fsrc * src_dir[c] : 0.0;
+        un[d] = 2.0 * u[d] - up[d] + dt * dt / mass[n] * (F - Kmu[d]);
+      }
+    for (int r = 0; r < n_rec; ++r)
+      for (int c = 0; c < 3; ++c)
+        tr[((int64_t)it * n_rec + r) * 3 + c] = un[3 * rec_nodes[r] + c];
+  }
+  double J = 0.0;
+  for (int64_t q = 0; q < 3 * (int64_t)n_rec * N; ++q) J += 0.5 * (tr[q] - data[q]) * (tr[q] - data[q]);
+  if (misfit) *misfit = J;
+  /* dK_e/dG at fixed kappa for each material's element size (same for all) */
+  if (oracle_element_stiffness(kind, ds, 0.0, 1.0, Kg)) goto done;
+  for (int64_t e = 0; e < ne; ++e) grad[e] = 0.0;
+  /* backward: m = N .. 1 produces mu^{m-1}; then the n = m-1 gradient term */
+  for (int m = N; m >= 1; --m) {
+    /* g = dJ/du^m: residual of trace row m-1 at the receiver nodes */
+    for (size_t q = 0; q < sz; ++q) g[q] = 0.0;
+    for (int r = 0; r < n_rec; ++r)
+      for (int c = 0; c < 3; ++c) {
+        int64_t q = ((int64_t)(m - 1) * n_rec + r) * 3 + c;
+        g[3 * rec_nodes[r] + c] += tr[q] - data[q];
+      }
+    if (oracle_ku(kind, nx, ny, nz, ds, mat, table, n_mat, 0, mu1, Kmu)) goto done;
+    for (int64_t n = 0; n < nn; ++n)
+      for (int c = 0; c < 3; ++c) {
+        int64_t d = 3 * n + c;
+        mu2[d] = fixed[n] ? 0.0
+                          : 2.0 * mu1[d] - mu0[d] - dt * dt / mass[n] * Kmu[d] - g[d] / mass[n];
+      }
+    /* dJ/dG_e += dt^2 mu^{m-1}_e . dK_e/dG u^{m-1}_e */
+    const double *u = U + sz * (m - 1);
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          int64_t e = i + (int64_t)nx * (j + (int64_t)ny * k);
+          if (mat[e] < 0) continue;
+          double ue[24], me[24];
+          for (int a = 0; a < 8; ++a) {
+            int64_t nd = node_id(nx, ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+            for (int c = 0; c < 3; ++c) { ue[3 * a + c] = u[3 * nd + c]; me[3 * a + c] = mu2[3 * nd + c]; }
+          }
+          double acc = 0.0;
+          for (int rr = 0; rr < 24; ++rr) {
+            double kr = 0.0;
+            for (int s2 = 0; s2 < 24; ++s2) kr += Kg[rr * 24 + s2] * ue[s2];
+            acc += me[rr] * kr;
+          }
+          grad[e] += dt * dt * acc;
+        }
+    double *t = mu0; mu0 = mu1; mu1 = mu2; mu2 = t;
+  }
+  rc = 0;
+done:
+  free(U); free(tr); free(mass); free(mu0); free(mu1); free(mu2); free(Kmu); free(g); free(Kg);
+  free(fixed);
+  return rc;
+}

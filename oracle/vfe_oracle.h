@@ -115,6 +115,22 @@ int oracle_run(int kind, int nx, int ny, int nz, double ds,
                const double *u0, const double *um1,
                double *traces, double *u_out, double *um1_out);
 
+/* Adjoint-state gradient of the receiver misfit
+ *   J = 1/2 sum_{n<N} sum_r |u^{n+1}(r) - data[n][r]|^2
+ * for the run of oracle_run (from rest), with respect to each element's shear
+ * modulus G_e at fixed kappa_e: with multipliers mu^n of the step equations,
+ *   mu^{m-1} = 2 mu^m - mu^{m+1} - dt^2 M^-1 K mu^m - M^-1 dJ/du^m,
+ *   mu^N = mu^{N+1} = 0, fixed DOFs zero, and
+ *   dJ/dG_e = dt^2 sum_{n=0}^{N-1} mu^n_e . (dK_e/dG) u^n_e.
+ * Stores every forward state (small meshes only).  grad: nx*ny*nz. */
+int oracle_misfit_gradient(int kind, int nx, int ny, int nz, double ds,
+                           const int32_t *mat, const double *table, int n_mat,
+                           int fix_bottom, double dt, int nsteps,
+                           int64_t src_node, const double *src_dir, double f0,
+                           double t0, double amp, int n_rec,
+                           const int64_t *rec_nodes, const double *data,
+                           double *grad, double *misfit);
+
 #ifdef __cplusplus
 }
 #endif

@@ -177,6 +177,8 @@ struct vfe_mesh {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_valid[2] = {false, false};
   int64_t gen = 0;  // bumped whenever kernel arguments change (batches rebuild)
+  double *d_inj = nullptr;  // injection array [rows][n_rec][3] (adjoint source)
+  std::vector<double> table;  // the caller's {Vp, Vs, rho} rows
 };
 
 static void invalidate_graphs(vfe_mesh *m) {
@@ -214,6 +216,7 @@ static TcDevice tc_device(const vfe_mesh *m, int cur) {
   d.traces = m->d_traces; d.or_slots = m->d_or; d.status = m->d_status;
   d.tiles_x = m->tiles_x; d.tiles_y = m->tiles_y;
   d.params = m->d_tcparams;
+  d.inj = m->d_inj;
   return d;
 }
 
@@ -225,6 +228,7 @@ static F64Device f64_device(const vfe_mesh *m, int cur) {
   d.u = m->d_u[cur]; d.u_prev = m->d_u[1 - cur]; d.u_next = m->d_u[1 - cur];
   d.dt2_m = m->d_dt2m; d.recv_nodes = m->d_recnodes; d.traces = m->d_traces;
   d.src_node = m->has_src ? m->src_node : -1;
+  d.inj = m->d_inj;
   return d;
 }
 
@@ -240,7 +244,7 @@ static int enqueue_step(vfe_mesh *m, int cur) {
     src.amp_scale = m->amp * m->src_scale;
     CUDA_TRY(tc_launch_prologue_ex(m->stream, m->d_tcparams, m->d_tcpersist, src, m->d_or,
                                    m->tiles_x * m->tiles_y, m->has_src ? 1 : 0, trace_on,
-                                   m->d_status));
+                                   m->d_status, m->d_inj, 3 * m->n_rec));
     TcDevice d = tc_device(m, cur);
     CUDA_TRY(tc_launch_step(m->stream, d, &m->tmap[cur], TC_MODE_STEP));
   } else {
@@ -308,7 +312,7 @@ int vfe_destroy(vfe_mesh *m) {
                   m->d_dt2m, m->d_K, m->d_recnodes, m->d_f64params, m->d_f64persist,
                   m->d_U[0], m->d_U[1], m->d_C, m->d_Bop, m->d_mats, m->d_recv,
                   m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist, m->d_segs,
-                  m->d_seg_off};
+                  m->d_seg_off, m->d_inj};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -368,6 +372,7 @@ int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_id
     m->rho[i] = rho;
   }
   m->mat.assign(material_ids, material_ids + m->ne);
+  m->table.assign(material_table, material_table + 3 * (size_t)n_materials);
   std::vector<char> used(n_materials, 0);
   for (int64_t e = 0; e < m->ne; ++e) {
     const int32_t v = m->mat[e];
@@ -471,7 +476,8 @@ static int build_f64(vfe_mesh *m) {
   CUDA_TRY(cudaMemcpy(m->d_dt2m, dt2m.data(), sizeof(double) * m->nn, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(m->d_u[0], 0, sizeof(double) * 3 * m->nn));
   CUDA_TRY(cudaMemset(m->d_u[1], 0, sizeof(double) * 3 * m->nn));
-  CUDA_TRY(cudaMemset(m->d_f64persist, 0, sizeof(int64_t) * 4));
+  const int64_t f64persist[4] = {0, 0, -1, 0};
+  CUDA_TRY(cudaMemcpy(m->d_f64persist, f64persist, sizeof(f64persist), cudaMemcpyHostToDevice));
   return VFE_OK;
 }
 
@@ -597,7 +603,7 @@ static int build_tc(vfe_mesh *m) {
   CUDA_TRY(cudaMemcpy(m->d_mats, mats.data(), sizeof(TcMaterial) * mats.size(),
                       cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(m->d_or, 0, sizeof(unsigned long long) * or_words));
-  int64_t persist[8] = {0, 0, 0, 0, (int64_t)(m->eC + m->e_ref), 0, 0, 0};
+  int64_t persist[8] = {0, 0, 0, 0, (int64_t)(m->eC + m->e_ref), 0, -1, 0};
   CUDA_TRY(cudaMemcpy(m->d_tcpersist, persist, sizeof(persist), cudaMemcpyHostToDevice));
   // TMA maps over the two state buffers: (x, y, z, component), int64, box 18x17x1x3
   EncodeTiledFn enc = encode_fn();
@@ -1222,6 +1228,8 @@ static int batch_build(vfe_batch *b) {
     A.ncols = m->tiles_x * m->tiles_y;
     A.have_src = m->has_src ? 1 : 0;
     A.trace_on = m->n_rec > 0 ? 1 : 0;
+    A.n_inj = 3 * m->n_rec;
+    A.inj = m->d_inj;
   }
   CUDA_TRY(cudaMalloc(&b->d_segs, sizeof(int4) * ns));
   CUDA_TRY(cudaMalloc(&b->d_seg_mesh, sizeof(int32_t) * ns));
@@ -1394,6 +1402,231 @@ int vfe_batch_synchronize(vfe_batch *b) {
     if (rc != VFE_OK) return rc;
   }
   return VFE_OK;
+}
+
+}  // extern "C"
+
+// ---- adjoint-state gradient of the receiver misfit ----------------------------
+
+namespace {
+
+struct Snapshot {  // a mesh's time-stepping state at one step
+  void *a = nullptr, *b = nullptr;  // u^n, u^{n-1} buffers
+  int64_t persist[8] = {0};
+  std::vector<unsigned long long> slots;
+  int cur = 0;
+  int64_t steps = 0, trace_rows = 0;
+};
+
+size_t state_bytes(const vfe_mesh *m) {
+  return m->opt.path == VFE_PATH_TC ? sizeof(int64_t) * 3 * m->comp : sizeof(double) * 3 * m->nn;
+}
+
+void *state_buf(vfe_mesh *m, int which) {
+  return m->opt.path == VFE_PATH_TC ? (void *)m->d_U[which] : (void *)m->d_u[which];
+}
+
+int64_t *persist_ptr(vfe_mesh *m) {
+  return m->opt.path == VFE_PATH_TC ? m->d_tcpersist : m->d_f64persist;
+}
+
+int persist_len(const vfe_mesh *m) { return m->opt.path == VFE_PATH_TC ? 8 : 4; }
+
+size_t slot_words(const vfe_mesh *m) { return 3 * (1 + (size_t)m->tiles_x * m->tiles_y); }
+
+int snap_save(vfe_mesh *m, Snapshot &s) {
+  const size_t sb = state_bytes(m);
+  if (!s.a) {
+    if (cudaMalloc(&s.a, sb) != cudaSuccess || cudaMalloc(&s.b, sb) != cudaSuccess)
+      return fail(VFE_ENOMEM, "checkpoint of %zu bytes", 2 * sb);
+  }
+  CUDA_TRY(cudaMemcpyAsync(s.a, state_buf(m, m->cur), sb, cudaMemcpyDeviceToDevice, m->stream));
+  CUDA_TRY(cudaMemcpyAsync(s.b, state_buf(m, 1 - m->cur), sb, cudaMemcpyDeviceToDevice, m->stream));
+  CUDA_TRY(cudaMemcpyAsync(s.persist, persist_ptr(m), sizeof(int64_t) * persist_len(m),
+                           cudaMemcpyDeviceToHost, m->stream));
+  if (m->opt.path == VFE_PATH_TC) {
+    s.slots.resize(slot_words(m));
+    CUDA_TRY(cudaMemcpyAsync(s.slots.data(), m->d_or, sizeof(unsigned long long) * s.slots.size(),
+                             cudaMemcpyDeviceToHost, m->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  s.cur = m->cur;
+  s.steps = m->steps;
+  s.trace_rows = m->trace_rows;
+  return VFE_OK;
+}
+
+int snap_restore(vfe_mesh *m, const Snapshot &s) {
+  const size_t sb = state_bytes(m);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->cur = s.cur;
+  CUDA_TRY(cudaMemcpyAsync(state_buf(m, m->cur), s.a, sb, cudaMemcpyDeviceToDevice, m->stream));
+  CUDA_TRY(cudaMemcpyAsync(state_buf(m, 1 - m->cur), s.b, sb, cudaMemcpyDeviceToDevice, m->stream));
+  CUDA_TRY(cudaMemcpyAsync(persist_ptr(m), s.persist, sizeof(int64_t) * persist_len(m),
+                           cudaMemcpyHostToDevice, m->stream));
+  if (m->opt.path == VFE_PATH_TC)
+    CUDA_TRY(cudaMemcpyAsync(m->d_or, s.slots.data(), sizeof(unsigned long long) * s.slots.size(),
+                             cudaMemcpyHostToDevice, m->stream));
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->steps = s.steps;
+  m->trace_rows = s.trace_rows;
+  return VFE_OK;
+}
+
+void snap_free(Snapshot &s) {
+  if (s.a) cudaFree(s.a);
+  if (s.b) cudaFree(s.b);
+  s.a = s.b = nullptr;
+}
+
+// back to rest at step 0 with empty traces; the injection stays off
+int rewind_mesh(vfe_mesh *m) {
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  const size_t sb = state_bytes(m);
+  CUDA_TRY(cudaMemset(state_buf(m, 0), 0, sb));
+  CUDA_TRY(cudaMemset(state_buf(m, 1), 0, sb));
+  if (m->opt.path == VFE_PATH_TC) {
+    const int64_t p[8] = {0, 0, 0, 0, (int64_t)(m->eC + m->e_ref), 0, -1, 0};
+    CUDA_TRY(cudaMemcpy(m->d_tcpersist, p, sizeof(p), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(m->d_or, 0, sizeof(unsigned long long) * slot_words(m)));
+  } else {
+    const int64_t p[4] = {0, 0, -1, 0};
+    CUDA_TRY(cudaMemcpy(m->d_f64persist, p, sizeof(p), cudaMemcpyHostToDevice));
+  }
+  m->cur = 0;
+  m->steps = 0;
+  m->trace_rows = 0;
+  return VFE_OK;
+}
+
+// per-step increments at the receivers from the mesh's current step on
+int set_injection(vfe_mesh *m, const double *host, int64_t rows) {
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (m->d_inj) cudaFree(m->d_inj);
+  m->d_inj = nullptr;
+  const size_t bytes = sizeof(double) * 3 * (size_t)m->n_rec * rows;
+  if (cudaMalloc(&m->d_inj, bytes) != cudaSuccess) return fail(VFE_ENOMEM, "injection array");
+  CUDA_TRY(cudaMemcpy(m->d_inj, host, bytes, cudaMemcpyHostToDevice));
+  const int64_t base = m->steps;
+  CUDA_TRY(cudaMemcpy(persist_ptr(m) + (m->opt.path == VFE_PATH_TC ? 6 : 2), &base,
+                      sizeof(int64_t), cudaMemcpyHostToDevice));
+  invalidate_graphs(m);
+  return VFE_OK;
+}
+
+// u^n of the mesh as FP64 [nn][3] on the device
+int state_to_f64(vfe_mesh *m, double *dst) {
+  if (m->opt.path == VFE_PATH_TC) {
+    CUDA_TRY(tc_state_to_f64(m->stream, m->d_U[m->cur], m->d_tcpersist, 0, m->nx, m->ny, m->nn,
+                             m->nxp, m->plane, m->comp, dst));
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(dst, m->d_u[m->cur], sizeof(double) * 3 * m->nn,
+                             cudaMemcpyDeviceToDevice, m->stream));
+  }
+  return VFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpoint_every,
+                        double *grad_G, double *misfit_out) {
+  if (!m || !data || !grad_G) return fail(VFE_EINVAL, "NULL argument");
+  if (nsteps < 1 || checkpoint_every < 1) return fail(VFE_EINVAL, "need nsteps, checkpoint >= 1");
+  if (m->n_rec < 1) return fail(VFE_ESTATE, "the misfit needs receivers");
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  const int N = nsteps, C = checkpoint_every, nr = m->n_rec;
+  const int nb = (N + C - 1) / C;
+  vfe_mesh *adj = nullptr;
+  std::vector<Snapshot> snaps(nb);
+  double *d_block = nullptr, *d_mu = nullptr, *d_grad = nullptr, *d_Kg = nullptr;
+  int rc = VFE_OK;
+  do {
+    // the adjoint runs on a twin mesh: same geometry, materials, dt and path,
+    // no source, the forward receivers as injection points
+    vfe_options o = m->opt;
+    o.dt = m->dt;
+    o.stream = m->stream;
+    if ((rc = vfe_create_mesh(m->nx, m->ny, m->nz, m->h, m->mat.data(), m->table.data(),
+                              m->n_mat, &o, &adj)) != VFE_OK)
+      break;
+    if ((rc = vfe_set_receivers(adj, nr, m->rec_ijk.data())) != VFE_OK) break;
+    // forward from rest with checkpoints every C steps
+    if ((rc = rewind_mesh(m)) != VFE_OK) break;
+    if ((rc = ensure_trace_capacity(m, N)) != VFE_OK) break;
+    for (int b = 0; b < nb && rc == VFE_OK; ++b) {
+      if ((rc = snap_save(m, snaps[b])) != VFE_OK) break;
+      rc = vfe_step(m, std::min(C, N - b * C));
+    }
+    if (rc != VFE_OK) break;
+    std::vector<double> tr((size_t)N * nr * 3);
+    int64_t rows = 0;
+    if ((rc = vfe_get_traces(m, tr.data(), &rows)) != VFE_OK) break;
+    // misfit and the adjoint source -M^-1 dJ/du^m, m = N - k for adjoint step k
+    double J = 0.0;
+    std::vector<double> inj((size_t)N * nr * 3, 0.0);
+    for (int n = 0; n < N; ++n)
+      for (int r = 0; r < nr; ++r) {
+        const int64_t node = m->rec_nodes[r];
+        for (int c = 0; c < 3; ++c) {
+          const size_t q = ((size_t)n * nr + r) * 3 + c;
+          const double res = tr[q] - data[q];
+          J += 0.5 * res * res;
+          const int k = N - 1 - n;  // residual of u^{n+1} drives mu^n: adjoint step k
+          if (!m->fixed[node]) inj[((size_t)k * nr + r) * 3 + c] = -res / m->mass[node];
+        }
+      }
+    if (misfit_out) *misfit_out = J;
+    if ((rc = rewind_mesh(adj)) != VFE_OK) break;
+    if ((rc = set_injection(adj, inj.data(), N)) != VFE_OK) break;
+    // dK_e/dG at fixed kappa
+    double Kg[576];
+    element_matrix(m->opt.element_kind, m->h, -2.0 / 3.0, 1.0, Kg);
+    const size_t fb = sizeof(double) * 3 * m->nn;
+    cudaError_t e;
+    if ((e = cudaMalloc(&d_block, fb * (C + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&d_mu, fb)) != cudaSuccess ||
+        (e = cudaMalloc(&d_grad, sizeof(double) * m->ne)) != cudaSuccess ||
+        (e = cudaMalloc(&d_Kg, sizeof(Kg))) != cudaSuccess) {
+      rc = fail(VFE_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
+      break;
+    }
+    CUDA_TRY(cudaMemset(d_grad, 0, sizeof(double) * m->ne));
+    CUDA_TRY(cudaMemcpy(d_Kg, Kg, sizeof(Kg), cudaMemcpyHostToDevice));
+    // backward over the blocks: recompute u^{s0..s0+len}, then adjoint steps
+    for (int b = nb - 1; b >= 0 && rc == VFE_OK; --b) {
+      const int s0 = b * C, len = std::min(C, N - s0);
+      if ((rc = snap_restore(m, snaps[b])) != VFE_OK) break;
+      if ((rc = state_to_f64(m, d_block)) != VFE_OK) break;
+      for (int j = 1; j <= len && rc == VFE_OK; ++j) {
+        if ((rc = vfe_step(m, 1)) != VFE_OK) break;
+        rc = state_to_f64(m, d_block + (size_t)j * 3 * m->nn);
+      }
+      for (int mi = s0 + len; mi >= s0 + 1 && rc == VFE_OK; --mi) {
+        if ((rc = vfe_step(adj, 1)) != VFE_OK) break;  // mu^{mi-1}
+        if ((rc = state_to_f64(adj, d_mu)) != VFE_OK) break;
+        const cudaError_t ge = grad_g_accumulate(
+            m->stream, m->nx, m->ny, m->nz, m->d_mat, d_Kg,
+            d_block + (size_t)(mi - 1 - s0) * 3 * m->nn, d_mu, m->dt * m->dt, d_grad);
+        if (ge != cudaSuccess) rc = fail(VFE_ECUDA, "gradient kernel: %s", cudaGetErrorString(ge));
+      }
+    }
+    if (rc != VFE_OK) break;
+    if ((rc = vfe_synchronize(adj)) != VFE_OK) break;
+    CUDA_TRY(cudaMemcpy(grad_G, d_grad, sizeof(double) * m->ne, cudaMemcpyDeviceToHost));
+    rc = rewind_mesh(m);
+  } while (0);
+  std::string msg = g_last_error;
+  for (auto &s : snaps) snap_free(s);
+  if (d_block) cudaFree(d_block);
+  if (d_mu) cudaFree(d_mu);
+  if (d_grad) cudaFree(d_grad);
+  if (d_Kg) cudaFree(d_Kg);
+  if (adj) vfe_destroy(adj);
+  g_last_error = msg;
+  return rc;
 }
 
 }  // extern "C"

@@ -12,10 +12,12 @@
 struct F64StepParams {
   int64_t step;
   int64_t trace_row;
+  int64_t inj_row;
   double src[3];
 };
 
-// persist[0] = step, [1] = trace rows
+// persist[0] = step, [1] = trace rows, [2] = first step of the injection
+// array (-1: none)
 __global__ void f64_prologue_kernel(F64StepParams *p, int64_t *persist, TcSource sd, int have_src,
                                     int trace_on) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -23,6 +25,7 @@ __global__ void f64_prologue_kernel(F64StepParams *p, int64_t *persist, TcSource
   F64StepParams q;
   q.step = n;
   q.trace_row = trace_on ? persist[1] : -1;
+  q.inj_row = persist[2] >= 0 ? n - persist[2] : -1;
   // F^n = amp ricker(n dt) dir
   const double fv = have_src ? sd.amp_scale * ricker_wavelet((double)n * sd.dt, sd.f0, sd.t0) : 0.0;
   q.src[0] = fv * sd.dir[0];
@@ -72,7 +75,14 @@ __global__ void __launch_bounds__(256) f64_step_kernel(const F64Device d, const 
     double un[3];
     for (int k = 0; k < 3; ++k) {
       const double F = src ? p.src[k] : 0.0;
-      un[k] = c == 0.0 ? 0.0 : 2.0 * d.u[3 * n + k] - d.u_prev[3 * n + k] + c * (F - fv[k]);
+      un[k] = 2.0 * d.u[3 * n + k] - d.u_prev[3 * n + k] + c * (F - fv[k]);
+    }
+    if (p.inj_row >= 0)  // injected increments at receiver nodes (adjoint source)
+      for (int r = 0; r < d.n_rec; ++r)
+        if (d.recv_nodes[r] == n)
+          for (int k = 0; k < 3; ++k) un[k] += d.inj[(p.inj_row * d.n_rec + r) * 3 + k];
+    for (int k = 0; k < 3; ++k) {
+      if (c == 0.0) un[k] = 0.0;
       d.u_next[3 * n + k] = un[k];
     }
     if (p.trace_row >= 0) {

@@ -37,6 +37,7 @@
 struct TcStepParams {     // written by the per-step prologue kernel
   int64_t step;           // global step index n (source time n*dt)
   int64_t trace_row;      // row of the trace buffer for this step (-1: none)
+  int64_t inj_row;        // row of the injection array for this step (-1: none)
   int64_t dU_src[3];      // source increment in the new fixed-point units
   int rs;                 // rescale: U_new units = old units * 2^rs
   int shq;                // digit shift: q = U_raw >> shq
@@ -86,6 +87,7 @@ struct TcDevice {         // everything the TC kernels read (by value)
   int tiles_x, tiles_y;
   int *status;            // device error flags (bit 0: wait timeout)
   const TcStepParams *params;
+  const double *inj;      // [rows][n_rec][3] displacement increments at the receivers
   int64_t *S_out;         // K u mode: per-node S (int64 x 3, SoA like U)
   int64_t *partials_out;  // partials mode: per element 48 int64 (element order)
 };
@@ -110,7 +112,8 @@ struct TcPrologueArgs {       // one mesh's inputs to the per-step prologue
   int *status;
   double amp_scale, dt, f0, t0;
   double dir[3];
-  int ncols, have_src, trace_on, pad;
+  int ncols, have_src, trace_on, n_inj;  // n_inj: values per injection row (3 n_rec)
+  const double *inj;                     // injection array (see TcDevice::inj)
 };
 
 // FP64 path ------------------------------------------------------------------
@@ -129,6 +132,7 @@ struct F64Device {
   double *traces;
   int64_t src_node;
   double *f_out;          // K u mode output
+  const double *inj;      // [rows][n_rec][3] displacement increments at the receivers
 };
 
 // Ricker point source (Section 3 applies an impulse force in z):
@@ -167,10 +171,18 @@ cudaError_t tc_prepare();
 cudaError_t f64_prepare();
 cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t *persist,
                                   const TcSource &src, unsigned long long *or_slots, int ncols,
-                                  int have_src, int trace_on, int *status);
+                                  int have_src, int trace_on, int *status, const double *inj,
+                                  int n_inj);
 cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
 cudaError_t tc_launch_batch_prologue(cudaStream_t s, const TcPrologueArgs *args, int n_meshes);
 cudaError_t tc_launch_batch_step(cudaStream_t s, const TcBatch &b, int stages);
+
+cudaError_t tc_state_to_f64(cudaStream_t s, const int64_t *U, const int64_t *persist,
+                            int extra_shift, int nx, int ny, int64_t nn, int nxp, int64_t plane,
+                            int64_t comp, double *out);
+cudaError_t grad_g_accumulate(cudaStream_t s, int nx, int ny, int nz, const int32_t *mat,
+                              const double *Kg, const double *u, const double *mu, double scale,
+                              double *grad);
 
 size_t f64_params_bytes();
 cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,

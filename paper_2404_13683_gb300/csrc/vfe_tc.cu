@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // receivers of this segment (the previous segment's reads are fenced by
     // the barriers of its last layer)
     int nrec = 0;
-    if (MODE == TC_MODE_STEP && d.n_rec > 0 && P.trace_row >= 0) {
+    if (MODE == TC_MODE_STEP && d.n_rec > 0 && (P.trace_row >= 0 || P.inj_row >= 0)) {
       const int32_t *roff = batched ? b.recv_off : d.recv_off;
       const TcRecv *rv = batched ? b.recv : d.recv;
       const int rbeg = roff[sg];
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         } else if (MODE == TC_MODE_STEP) {
           const int64_t *ucur = uslot + (L & 3) * (kUSlotStride / 8);
           const bool is_src = (nidx == d.src_node);
-          int64_t unew[3];
+          int64_t unew[3], uold[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const int64_t u0 =
@@ -669,21 +669,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             int64_t un = 2 * u0 - um - du;
             if (is_src) un += P.dU_src[c];
-            if (cn == 0) un = 0;  // fixed or massless node
             unew[c] = un;
-            d.U_next[c * d.comp + nidx] = un;
-            // the slot bounds u^{n+1} and u^n (both in the new units)
-            or_seg |= (unsigned long long)(un < 0 ? -un : un) |
-                      (unsigned long long)(u0 < 0 ? -u0 : u0);
+            uold[c] = u0;
           }
-          for (int r = 0; r < nrec; ++r) {
-            const TcRecv rv = srecv[r];
-            if (rv.ei == ei && rv.ej == ej && rv.k == L) {
-              double *out = d.traces + (P.trace_row * d.n_rec + rv.r) * 3;
+          // injected increments at receiver nodes (the adjoint's residual source)
+          if (P.inj_row >= 0)
+            for (int r = 0; r < nrec; ++r) {
+              const TcRecv rv = srecv[r];
+              if (rv.ei == ei && rv.ej == ej && rv.k == L) {
+                const double *iv = d.inj + (P.inj_row * d.n_rec + rv.r) * 3;
 #pragma unroll
-              for (int c = 0; c < 3; ++c) out[c] = ldexp((double)unew[c], -P.F);
+                for (int c = 0; c < 3; ++c) unew[c] += llrint(ldexp(iv[c], P.F));
+              }
             }
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if (cn == 0) unew[c] = 0;  // fixed or massless node
+            d.U_next[c * d.comp + nidx] = unew[c];
+            // the slot bounds u^{n+1} and u^n (both in the new units)
+            or_seg |= (unsigned long long)(unew[c] < 0 ? -unew[c] : unew[c]) |
+                      (unsigned long long)(uold[c] < 0 ? -uold[c] : uold[c]);
           }
+          if (P.trace_row >= 0)
+            for (int r = 0; r < nrec; ++r) {
+              const TcRecv rv = srecv[r];
+              if (rv.ei == ei && rv.ej == ej && rv.k == L) {
+                double *out = d.traces + (P.trace_row * d.n_rec + rv.r) * 3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[c] = ldexp((double)unew[c], -P.F);
+              }
+            }
         }
       }
     }
@@ -713,7 +728,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // per-step prologue: rescale decision, digit shift, source increment
 // ---------------------------------------------------------------------------
 // persist[0] = F of u^n, [1] = step, [2] = trace rows, [4] = eC + e_ref,
-// [5] = shift of the last step (u^{n-1} has F + [5])
+// [5] = shift of the last step (u^{n-1} has F + [5]), [6] = first step of the
+// injection array (-1: none)
 // One mesh's prologue, run by a block (thread 0 does the scalar work).
 __device__ void prologue_body(const TcPrologueArgs &A) {
   int64_t *persist = A.persist;
@@ -745,6 +761,16 @@ __device__ void prologue_body(const TcPrologueArgs &A) {
       bs_valid = true;
     }
   }
+  if (persist[6] >= 0 && A.inj) {  // injected increments count like the source
+    const double *row = A.inj + (n - persist[6]) * A.n_inj;
+    double mx = 0.0;
+    for (int i = 0; i < A.n_inj; ++i) mx = fmax(mx, fabs(row[i]));
+    if (mx > 0.0) {
+      const int bi = ilogb(mx) + F_old + 1;
+      bs = bs_valid ? max(bs, bi) : bi;
+      bs_valid = true;
+    }
+  }
   int rs = 0;
   if (orp || bs_valid) {
     const int bb = orp ? (bs_valid ? max(b, bs) : b) : bs;
@@ -756,6 +782,7 @@ __device__ void prologue_body(const TcPrologueArgs &A) {
   TcStepParams p;
   p.step = n;
   p.trace_row = A.trace_on ? persist[2] : -1;
+  p.inj_row = persist[6] >= 0 ? n - persist[6] : -1;
   for (int c = 0; c < 3; ++c) p.dU_src[c] = A.have_src ? llrint(ldexp(src[c], F_new)) : 0;
   p.rs = rs;
   p.shq = shq;
@@ -774,7 +801,8 @@ __device__ void prologue_body(const TcPrologueArgs &A) {
 }
 
 // persist[0] = F of u^n, [1] = step, [2] = trace rows, [4] = eC + e_ref,
-// [5] = shift of the last step (u^{n-1} has F + [5])
+// [5] = shift of the last step (u^{n-1} has F + [5]), [6] = first step of the
+// injection array (-1: none)
 __global__ void tc_prologue_kernel(const TcPrologueArgs A) { prologue_body(A); }
 
 __global__ void tc_batch_prologue_kernel(const TcPrologueArgs *args) {
@@ -785,7 +813,8 @@ int tc_smem_bytes() { return kSmemBytes; }
 
 cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t *persist,
                                   const TcSource &src, unsigned long long *or_slots, int ncols,
-                                  int have_src, int trace_on, int *status) {
+                                  int have_src, int trace_on, int *status, const double *inj,
+                                  int n_inj) {
   TcPrologueArgs A;
   A.params = params;
   A.persist = persist;
@@ -799,7 +828,8 @@ cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t 
   A.ncols = ncols;
   A.have_src = have_src;
   A.trace_on = trace_on;
-  A.pad = 0;
+  A.n_inj = n_inj;
+  A.inj = inj;
   tc_prologue_kernel<<<1, 256, 0, s>>>(A);
   return cudaGetLastError();
 }

@@ -34,6 +34,7 @@ EXPORTS = (
     "vfe_get_state", "vfe_set_state", "vfe_last_error", "vfe_debug_tc_partials",
     "vfe_get_trace_rows", "vfe_internal_force_noalloc",
     "vfe_create_batch", "vfe_batch_step", "vfe_batch_synchronize", "vfe_destroy_batch",
+    "vfe_misfit_gradient",
 )
 
 
@@ -78,6 +79,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_internal_force.argtypes = [P, P, P]
     L.vfe_internal_force_noalloc.argtypes = [P, P, P]
     L.vfe_create_batch.argtypes = [I, P, ctypes.POINTER(ctypes.c_void_p)]
+    L.vfe_misfit_gradient.argtypes = [P, I, P, I, P, ctypes.POINTER(D)]
     L.vfe_batch_step.argtypes = [P, I]
     L.vfe_batch_synchronize.argtypes = [P]
     L.vfe_destroy_batch.argtypes = [P]
@@ -236,6 +238,18 @@ def vfe_debug_tc_partials(mesh, u, element_ids):
     return out, sh.value, fb.value
 
 
+def vfe_misfit_gradient(mesh, data, checkpoint_every=100):
+    """(dJ/dG per element, J) for a run of len(data) steps from rest."""
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    nsteps = data.shape[0]
+    _, ne = vfe_get_sizes(mesh)
+    grad = np.zeros(ne)
+    J = ctypes.c_double()
+    _check(load().vfe_misfit_gradient(mesh, int(nsteps), _p(data), int(checkpoint_every),
+                                      _p(grad), ctypes.byref(J)))
+    return grad, J.value
+
+
 def vfe_create_batch(handles):
     arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
                                              for h in handles])
@@ -292,9 +306,11 @@ class Mesh:
     """Owning wrapper over a ``vfe_mesh*`` built from a workload dictionary
     (see ``workloads.py``)."""
 
-    def __init__(self, workload, path=VFE_PATH_TC, kind=VFE_OVFEM, stages=5, dt=0.0,
+    def __init__(self, workload, path=VFE_PATH_TC, kind=VFE_OVFEM, stages=5, dt=None,
                  fix_bottom=True, stream=None, device=0, source=True, receivers=True):
         nx, ny, nz = workload["shape"]
+        if dt is None:
+            dt = float(workload.get("dt", 0.0))
         opt = vfe_default_options(element_kind=kind, path=path, stages=stages, dt=dt,
                                   fix_bottom=int(fix_bottom), device=device,
                                   stream=stream or 0)

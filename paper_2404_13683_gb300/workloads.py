@@ -17,6 +17,16 @@ below stand in for it:
 * ``config4``: 64 independent cubic models, n ~ U{32..128} (seeded), three
   random layers each, random source node and frequency (3-10 Hz), 1,000
   steps each -- the many-case batch.
+* ``config5``: 96^3, two layers and a hidden spherical low-velocity anomaly
+  (diameter 12 cells, Vs -30 %) at the centre, 36 surface receivers (6 x 6),
+  1,500 steps -- the adjoint-gradient workload (``anomaly=False`` gives the
+  background model whose misfit gradient is sought).
+* ``paper_rebar``: the shape of the paper's experiment (Section 3): a
+  324 x 128 x 384 mm concrete block at ds = 2 mm (162 x 64 x 192 voxels) with a
+  steel rebar of radius 15 mm along y at x = 160, z = 100 mm, the source and
+  the eight observation points of Table 1, dt = 5e-8 s, 16,384 steps.  The
+  paper gives no material constants; typical concrete (Vp 4000, Vs 2400,
+  rho 2300) and steel (5900, 3200, 7850) values stand in.
 * ``random_mesh``: small random meshes with voids for parity tests.
 """
 from __future__ import annotations
@@ -133,6 +143,38 @@ def config4(seed: int = 4, n_models: int = 64, n_min: int = 32, n_max: int = 128
                             _source(src, float(rng.uniform(3.0, 10.0))), rec, 1000,
                             "config4_model%02d_%d" % (i, n)))
     return models
+
+
+def config5(anomaly: bool = True, n: int = 96, nsteps: int = 1500):
+    """Two layers with (or without) a spherical low-velocity anomaly."""
+    kk, jj, ii = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    table = [[1500.0, 600.0, 1900.0], [2500.0, 1000.0, 2100.0], [2500.0, 700.0, 2100.0]]
+    mat = np.where(kk >= n // 2, 0, 1)
+    if anomaly:
+        r = n / 8.0
+        c = n / 2.0
+        sphere = ((ii + 0.5 - c) ** 2 + (jj + 0.5 - c) ** 2 + (kk + 0.5 - c) ** 2) <= r * r
+        mat = np.where(sphere, 2, mat)
+    step = n // 6
+    rec = [(step // 2 + a * step, step // 2 + b * step, n) for b in range(6) for a in range(6)]
+    return _mesh((n, n, n), 1.0, mat, table, _source((n // 2, n // 2, n), 20.0), rec, nsteps,
+                 "config5_%d%s" % (n, "_anomaly" if anomaly else "_background"))
+
+
+def paper_rebar():
+    """Concrete block with a rebar, sized like the paper's ultrasonic model."""
+    ds = 2e-3
+    nx, ny, nz = 162, 64, 192
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    xc, zc = (ii + 0.5) * ds, (kk + 0.5) * ds
+    rebar = (xc - 0.160) ** 2 + (zc - 0.100) ** 2 <= 0.015 ** 2
+    mat = np.where(rebar, 1, 0)
+    table = [[4000.0, 2400.0, 2300.0], [5900.0, 3200.0, 7850.0]]
+    src = _source((78, 36, 192), 112.5e3, 4.096e-4)
+    rec = [(int(round(x / 2.0)), 30, 192) for x in (26, 60, 108, 144, 180, 216, 264, 300)]
+    w = _mesh((nx, ny, nz), ds, mat, table, src, rec, 16384, "paper_rebar_162x64x192")
+    w["dt"] = 5e-8
+    return w
 
 
 def random_mesh(seed: int, shape=None, n_mat: int = 3, void_frac: float = 0.1, h=None):
