@@ -143,17 +143,21 @@ __device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo, uin
   return d;
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                        uint32_t accumulate) {
+// Issued by every lane of a converged warp; one elected lane executes the
+// instruction, so descriptors formed as a base plus constants can stay in
+// uniform registers (the issue then keeps pace with the tensor pipe).
+__device__ __forceinline__ void mma_f16_elect(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t accumulate) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+__device__ __forceinline__ void mma_commit_elect(uint64_t *bar) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
           smem_u32(bar))
       : "memory");
 }
@@ -172,16 +176,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r) {
                : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -195,12 +189,6 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// floor(v / 2^s) for s >= 0, v * 2^-s for s < 0.  Left shifts only occur
-// when the prologue has checked that the result fits (|v| 2^-s < 2^59).
-__device__ __forceinline__ int64_t shr_floor(int64_t v, int s) {
-  if (s >= 0) return v >> min(s, 63);
-  return (int64_t)((uint64_t)v << min(-s, 63));
-}
 // round(v / 2^s), halves toward +inf, for |v| < 2^62; v * 2^-s for s <= 0
 __device__ __forceinline__ int64_t shr_round(int64_t v, int s) {
   if (s <= 0) return (int64_t)((uint64_t)v << min(-s, 63));
@@ -212,9 +200,6 @@ __device__ __forceinline__ int64_t shr_round(int64_t v, int s) {
 __device__ __forceinline__ float int_to_f32_exact(int d) {
   return __int_as_float(TC_MAGIC_BITS + d) - 12582912.0f;
 }
-
-// exact integer from a magic-biased fp32 accumulator word
-__device__ __forceinline__ int acc_to_int(uint32_t w) { return (int)w - TC_MAGIC_BITS; }
 
 }  // namespace
 
@@ -287,7 +272,7 @@ __device__ __forceinline__ int64_t mul2_hi63(int64_t P, int64_t Q, int A1, int A
 // 15x15 node column (tx, ty) and a range of owned node planes [z0, z1).  The
 // host balances column-planes across CTAs, so every SM gets the same work.
 // ---------------------------------------------------------------------------
-template <int MODE, int STAGES>
+template <int MODE, int STAGES, bool BATCHED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_step_kernel(const __grid_constant__ CUtensorMap tmap_u, const TcDevice d0,
                    const TcBatch b) {
@@ -305,7 +290,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const bool batched = b.devs != nullptr;
+  // a single mesh reads its arguments straight from the kernel parameters
+  constexpr bool batched = BATCHED;
   // with fewer stages the low digits are dropped (the top ones carry the value)
   constexpr int s_lo = TC_MAX_STAGES - STAGES;
 
@@ -348,7 +334,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // all 512 columns are allocated, so the allocation starts at lane 0, column 0
   const uint32_t tmem_base = misc[0];
+  if (tmem_base != 0u) {  // cannot happen; fail loudly rather than use wrong columns
+    if (tid == 0) atomicOr(batched ? b.devs[0].status : d0.status, 4);
+    __syncthreads();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                   "r"(kTmemCols));
+    return;
+  }
 
   uint32_t uphase = 0;   // parity bit per U slot
   uint32_t mma_phase = 0;
@@ -482,25 +477,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // they are formed by adding offsets to one base descriptor.
     const uint64_t adesc0 = make_sdesc(smem_u32(digits), 2 * kBlockBytes, kBlockBytes);
     const uint64_t bdesc0 = make_sdesc(smem_u32(bop), 6 * kBlockBytes, kBlockBytes);
+    // warp t issues the MMAs of tile t (both warps are converged here)
     auto issue_mma = [&](int L) {
-      if (tid == 0) {
-        tc_fence_after();
-        const int sl0 = ((L % kDigitSlots) + kDigitSlots) % kDigitSlots;
-        const int sl1 = sl0 == kDigitSlots - 1 ? 0 : sl0 + 1;
-        const uint64_t a0 = adesc0 + (uint64_t)((sl0 * kDigitSlotBytes) >> 4);
-        const uint64_t a1 = adesc0 + (uint64_t)((sl1 * kDigitSlotBytes) >> 4);
+      if (warp >= 2) return;
+      tc_fence_after();
+      const int sl0 = ((L % kDigitSlots) + kDigitSlots) % kDigitSlots;
+      const int sl1 = sl0 == kDigitSlots - 1 ? 0 : sl0 + 1;
+      const uint64_t a0 = adesc0 + (uint64_t)((sl0 * kDigitSlotBytes + 16 * warp * kBlockBytes) >> 4);
+      const uint64_t a1 = adesc0 + (uint64_t)((sl1 * kDigitSlotBytes + 16 * warp * kBlockBytes) >> 4);
+      const uint32_t tcol = (uint32_t)(warp * kTileCols);
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-#pragma unroll
-          for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
-            const uint32_t dcol = tmem_base + (uint32_t)(t * kTileCols + s * TC_N);
-            const uint64_t off = (uint64_t)((s * kStageBytes + 16 * t * kBlockBytes) >> 4);
-            mma_f16(dcol, a0 + off, bdesc0, 0);
-            mma_f16(dcol, a1 + off, bdesc0 + (uint64_t)((2 * 6 * kBlockBytes) >> 4), 1);
-          }
-          mma_commit(&bars[4 + t]);
-        }
+      for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
+        const uint64_t off = (uint64_t)((s * kStageBytes) >> 4);
+        mma_f16_elect(tcol + (uint32_t)(s * TC_N), a0 + off, bdesc0, 0);
+        mma_f16_elect(tcol + (uint32_t)(s * TC_N), a1 + off,
+                      bdesc0 + (uint64_t)((2 * 6 * kBlockBytes) >> 4), 1);
       }
+      mma_commit_elect(&bars[4 + warp]);
     };
 
     // ---- segment prologue: planes Z0-1, Z0, Z0+1 ---------------------------
@@ -517,10 +510,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     issue_mma(Lfirst);
 
+    // material id of this thread's element, loaded one layer ahead
+    auto mat_at = [&](int L) -> int {
+      return (elem_xy && L >= 0 && L < d.nz)
+                 ? d.mat[(int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L)]
+                 : -1;
+    };
+    int m_next = mat_at(Lfirst);
     for (int L = Lfirst; L <= Llast; ++L) {
-      int m = -1;
-      if (elem_xy && L >= 0 && L < d.nz)
-        m = d.mat[(int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L)];
+      const int m = m_next;
+      m_next = mat_at(L + 1);
       int64_t uprev[3] = {0, 0, 0}, cn = 0;
       const bool upd = (MODE == TC_MODE_STEP) && updater && L >= Z0;
       const int64_t nidx = (int64_t)L * d.plane + (int64_t)gj * d.nxp + gi;
@@ -839,39 +838,40 @@ cudaError_t tc_launch_batch_prologue(cudaStream_t s, const TcPrologueArgs *args,
   return cudaGetLastError();
 }
 
-template <int MODE, int S>
+template <int MODE, int S, bool BATCHED>
 static cudaError_t set_attr() {
-  return cudaFuncSetAttribute(tc_step_kernel<MODE, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kSmemBytes);
+  return cudaFuncSetAttribute(tc_step_kernel<MODE, S, BATCHED>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
-template <int MODE>
+template <int MODE, bool BATCHED>
 static cudaError_t set_attr_all() {
   cudaError_t e;
-  if ((e = set_attr<MODE, 1>()) != cudaSuccess) return e;
-  if ((e = set_attr<MODE, 2>()) != cudaSuccess) return e;
-  if ((e = set_attr<MODE, 3>()) != cudaSuccess) return e;
-  if ((e = set_attr<MODE, 4>()) != cudaSuccess) return e;
-  return set_attr<MODE, 5>();
+  if ((e = set_attr<MODE, 1, BATCHED>()) != cudaSuccess) return e;
+  if ((e = set_attr<MODE, 2, BATCHED>()) != cudaSuccess) return e;
+  if ((e = set_attr<MODE, 3, BATCHED>()) != cudaSuccess) return e;
+  if ((e = set_attr<MODE, 4, BATCHED>()) != cudaSuccess) return e;
+  return set_attr<MODE, 5, BATCHED>();
 }
 
 cudaError_t tc_prepare() {
   cudaError_t e;
-  if ((e = set_attr_all<TC_MODE_STEP>()) != cudaSuccess) return e;
-  if ((e = set_attr_all<TC_MODE_KU>()) != cudaSuccess) return e;
-  return set_attr_all<TC_MODE_PARTIALS>();
+  if ((e = set_attr_all<TC_MODE_STEP, false>()) != cudaSuccess) return e;
+  if ((e = set_attr_all<TC_MODE_STEP, true>()) != cudaSuccess) return e;
+  if ((e = set_attr_all<TC_MODE_KU, false>()) != cudaSuccess) return e;
+  return set_attr_all<TC_MODE_PARTIALS, false>();
 }
 
-template <int MODE>
+template <int MODE, bool BATCHED>
 static cudaError_t launch_mode(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap,
                                const TcBatch &b, int stages, int n_ctas) {
   const dim3 grid(n_ctas), block(TC_THREADS);
   switch (stages) {
-    case 1: tc_step_kernel<MODE, 1><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
-    case 2: tc_step_kernel<MODE, 2><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
-    case 3: tc_step_kernel<MODE, 3><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
-    case 4: tc_step_kernel<MODE, 4><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
-    default: tc_step_kernel<MODE, 5><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    case 1: tc_step_kernel<MODE, 1, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    case 2: tc_step_kernel<MODE, 2, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    case 3: tc_step_kernel<MODE, 3, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    case 4: tc_step_kernel<MODE, 4, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    default: tc_step_kernel<MODE, 5, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
   }
   return cudaGetLastError();
 }
@@ -880,9 +880,10 @@ cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap 
   TcBatch none;
   memset(&none, 0, sizeof(none));
   switch (mode) {
-    case TC_MODE_STEP: return launch_mode<TC_MODE_STEP>(s, d, tmap, none, d.stages, d.n_ctas);
-    case TC_MODE_KU: return launch_mode<TC_MODE_KU>(s, d, tmap, none, d.stages, d.n_ctas);
-    default: return launch_mode<TC_MODE_PARTIALS>(s, d, tmap, none, d.stages, d.n_ctas);
+    case TC_MODE_STEP:
+      return launch_mode<TC_MODE_STEP, false>(s, d, tmap, none, d.stages, d.n_ctas);
+    case TC_MODE_KU: return launch_mode<TC_MODE_KU, false>(s, d, tmap, none, d.stages, d.n_ctas);
+    default: return launch_mode<TC_MODE_PARTIALS, false>(s, d, tmap, none, d.stages, d.n_ctas);
   }
 }
 
@@ -893,5 +894,5 @@ cudaError_t tc_launch_batch_step(cudaStream_t s, const TcBatch &b, int stages) {
   memset(&none, 0, sizeof(none));
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof(dummy));
-  return launch_mode<TC_MODE_STEP>(s, none, &dummy, b, stages, b.n_ctas);
+  return launch_mode<TC_MODE_STEP, true>(s, none, &dummy, b, stages, b.n_ctas);
 }
