@@ -25,13 +25,15 @@
 //
 // Tiling: a CTA owns 15 x 15 node columns in x-y and a chunk of node planes in
 // z, computes the 16 x 16 elements per layer that touch them (one element of
-// halo), and marches up in z.  Per layer: TMA brings the next node plane into
-// shared memory, threads digitise it into the MN-major operand layout the
-// tensor core reads directly (no im2col), one thread issues 2 tiles x stages x
-// 2 MMAs (M=128, N=48, K=16), the 256 threads read their element's 48 x
-// stages accumulators from TMEM, recombine, apply the element's material,
-// reduce to nodes (warp shuffle in x, shared memory in y, registers in z) and
-// update their node.
+// halo), and marches up in z.  TMA brings node planes into a ring of shared
+// memory slots four planes ahead.  Per element layer L: two warps issue the
+// MMAs of its two M = 128 tiles (2 x stages x 2 MMAs, M=128, N=48, K=16) on
+// digit planes L and L+1, written beforehand in the MN-major operand layout
+// the tensor core reads directly (no im2col); the 512 threads read their
+// element's 48 x stages accumulators from TMEM, recombine, apply the element's
+// material and reduce to nodes (warp shuffle in x, shared memory in y,
+// registers in z).  After the one CTA barrier of the layer, half of the
+// threads update node plane L while the other half digitises plane L+3.
 #include <cuda_fp16.h>
 
 #include <cstring>
@@ -49,9 +51,9 @@ constexpr int kDigitSlotBytes = TC_MAX_STAGES * kStageBytes;
 constexpr int kDigitSlots = 3;
 constexpr int kUSlotBytes = 3 * TC_NODES * TC_BOXX * 8;   // TMA box (18,17,1,3) int64
 constexpr int kUSlotStride = (kUSlotBytes + 127) / 128 * 128;  // TMA smem dst: 128-B aligned
-constexpr int kUSlots = 4;
+constexpr int kUSlots = 8;                                 // node planes L .. L+4 in use
 constexpr int kBopBytes = TC_N * 32 * 2;
-constexpr int kYbufBytes = 2 * TC_EX * TC_EX * 3 * 8;
+constexpr int kYbufBytes = 2 * 2 * TC_EX * TC_EX * 3 * 8;  // half x layer parity
 constexpr int kCbufBytes = 2 * TC_EX * TC_EX * 3 * 8;     // z carry, double buffered
 
 constexpr int kOffDigits = 0;
@@ -63,7 +65,7 @@ constexpr int kOffMat = kOffCbuf + kCbufBytes;
 constexpr int kOffRecv = kOffMat + TC_MAX_MAT * (int)sizeof(TcMaterial);
 constexpr int kOffDev = kOffRecv + TC_MAX_REC_CTA * (int)sizeof(TcRecv);
 constexpr int kOffBar = kOffDev + ((int)sizeof(TcDevice) + 15) / 16 * 16;
-constexpr int kOffMisc = kOffBar + 8 * 8;
+constexpr int kOffMisc = kOffBar + 16 * 8;
 constexpr int kSmemUsed = kOffMisc + 64;
 // padded so that only one CTA fits per SM (it allocates 512 TMEM columns)
 constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
@@ -166,6 +168,12 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t &a, uint32_t &
                                          uint32_t &d) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
                : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t &a, uint32_t &b) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+               : "=r"(a), "=r"(b)
                : "r"(taddr));
 }
 
@@ -285,11 +293,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   TcMaterial *smat = reinterpret_cast<TcMaterial *>(smem + kOffMat);
   TcRecv *srecv = reinterpret_cast<TcRecv *>(smem + kOffRecv);
   TcDevice *sdev = reinterpret_cast<TcDevice *>(smem + kOffDev);  // batch: current mesh
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..3: U slots, 4,5: MMA tiles
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..7: U slots, 8,9: MMA tiles
   uint32_t *misc = reinterpret_cast<uint32_t *>(smem + kOffMisc);  // [0] tmem base, [1] abort
 
   const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
+  // the warp index broadcast from lane 0 is provably warp-uniform, so TMEM
+  // addresses and MMA descriptors derived from it live in uniform registers
+  const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0), lane = tid & 31;
   // a single mesh reads its arguments straight from the kernel parameters
   constexpr bool batched = BATCHED;
   // with fewer stages the low digits are dropped (the top ones carry the value)
@@ -307,8 +317,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (tid == 0) {
     misc[1] = 0;
     for (int i = 0; i < kUSlots; ++i) mbar_init(&bars[i], 1);
-    mbar_init(&bars[4], 1);
-    mbar_init(&bars[5], 1);
+    mbar_init(&bars[8], 1);
+    mbar_init(&bars[9], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -398,31 +408,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int i = tid; i < nrec; i += TC_THREADS) srecv[i] = rv[rbeg + i];
     }
 
-    auto issue_plane = [&](int p) {  // TMA of node plane p into U slot p & 3
-      if (tid == 0) {
-        const int s = p & 3;
+    auto issue_plane = [&](int p, int issuer) {  // TMA of node plane p into U slot p & 7
+      if (tid == issuer) {
+        const int s = p & 7;
         mbar_expect_tx(&bars[s], kUSlotBytes);
         tma_load_u(uslot + s * (kUSlotStride / 8), tmap, &bars[s], xbox, Y0, p);
       }
     };
-    auto wait_plane = [&](int p) -> bool {
-      const int s = p & 3;
-      const bool ok = mbar_wait(&bars[s], (uphase >> s) & 1u);
+    // every thread tracks the phase of every U slot; only the threads that
+    // read a plane's slot wait on it
+    auto wait_plane = [&](int p, bool do_wait) -> bool {
+      const int s = p & 7;
+      const bool ok = do_wait ? mbar_wait(&bars[s], (uphase >> s) & 1u) : true;
       uphase ^= 1u << s;
       return ok;
     };
-    // digitise node plane p into digit slot p mod 3: one task per (row,
-    // x-chunk, component, stage) writes the dx = 0 and dx = 1 lines.  With the
-    // offset-binary bias boff = sum_s 1024 2^(11 s), digit s of q = floor(U/2^shq)
-    // is ((q + boff) >> 11 s) & 2047 - 1024; q + boff is positive and below
-    // 2^55 because |q| < 2^51.
-    constexpr int ntask = TC_NODES * 6 * STAGES;
-    const int dtask = tid < ntask ? tid : -1;
-    const int ds_ = s_lo + (dtask < 0 ? 0 : dtask / (TC_NODES * 6));
-    const int dr_ = dtask < 0 ? 0 : dtask % (TC_NODES * 6);
-    const int dnj = dr_ / 6, dxc = (dr_ % 6) / 3, dc = dr_ % 3;
-    const int dsrc = (dc * TC_NODES + dnj) * TC_BOXX + 8 * dxc + xo;
-    const int ddst = ds_ * kStageBytes + (dnj * 2 + dxc) * kBlockBytes + dc * 16;
+    // digitise node plane p into digit slot p mod 3.  One task per (node row,
+    // node pair, component) shifts three node values once and writes, for
+    // every stage, the 32-bit word of the pair in the dx = 0 line (nodes 2k,
+    // 2k+1) and in the dx = 1 line (nodes 2k+1, 2k+2).  With the offset-binary
+    // bias boff = sum_s 1024 2^(11 s), digit s of q = floor(U/2^shq) is
+    // ((q + boff) >> 11 s) & 2047 - 1024; q + boff is positive and below 2^55
+    // because |q| < 2^51.  The float of that digit is exact: the bits
+    // 0x4B000000 | x are 2^23 + x, and subtracting 2^23 + 1024 leaves x - 1024.
+    constexpr int ntask = TC_NODES * 8 * 3;
     // digit quantum of this segment (Eq. intscaling, per node column): the
     // step uses the max |u| over the 3x3 node columns around the segment's
     // column (its elements' nodes) from the previous step, never more than the
@@ -443,31 +452,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // S of this segment is in units 2^(63 - e_ref + shq) of the raw state
     const int Rseg = P.eCref + P.rs - shq - 63;
     const int64_t dbias = (1LL << 10) | (1LL << 21) | (1LL << 32) | (1LL << 43) | (1LL << 54);
-    const int dshift = TC_DIGIT_BITS * ds_;
     unsigned long long or_seg = 0;
-    auto digitise = [&](int p) {
-      if (dtask < 0) return;
-      const int64_t *src = uslot + (p & 3) * (kUSlotStride / 8) + dsrc;
-      unsigned char *dst =
-          digits + ((p % kDigitSlots + kDigitSlots) % kDigitSlots) * kDigitSlotBytes + ddst;
-      float f[9];
+    auto digitise_task = [&](int p, int t) {
+      const int dk = t & 7;         // node pair in the row
+      const int dc = (t >> 3) % 3;  // component
+      const int dnj = t / 24;       // node row
+      const int64_t *src = uslot + (p & 7) * (kUSlotStride / 8) +
+                           (dc * TC_NODES + dnj) * TC_BOXX + 2 * dk + xo;
+      unsigned char *dst = digits + ((p % kDigitSlots + kDigitSlots) % kDigitSlots) * kDigitSlotBytes +
+                           (dnj * 2 + (dk >> 2)) * kBlockBytes + dc * 16 + (dk & 3) * 4;
+      uint64_t v[3];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const uint64_t v = (uint64_t)((src[i] >> shq) + dbias);
-        f[i] = int_to_f32_exact((int)((uint32_t)(v >> dshift) & 2047u) - 1024);
+      for (int i = 0; i < 3; ++i) v[i] = (uint64_t)((src[i] >> shq) + dbias);
+#pragma unroll
+      for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
+        float f[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          f[i] = __int_as_float((int)(((uint32_t)(v[i] >> (TC_DIGIT_BITS * s)) & 2047u) |
+                                      0x4B000000u)) - 8389632.0f;
+        const __half2 lo = __floats2half2_rn(f[0], f[1]);
+        const __half2 hi = __floats2half2_rn(f[1], f[2]);
+        *reinterpret_cast<__half2 *>(dst + s * kStageBytes) = lo;
+        *reinterpret_cast<__half2 *>(dst + s * kStageBytes + 48) = hi;
       }
-      uint4 lo, hi;  // dx = 0 line: nodes 0..7, dx = 1 line: nodes 1..8
-      __half2 h;
-      h = __floats2half2_rn(f[0], f[1]); lo.x = *reinterpret_cast<uint32_t *>(&h);
-      h = __floats2half2_rn(f[2], f[3]); lo.y = *reinterpret_cast<uint32_t *>(&h);
-      h = __floats2half2_rn(f[4], f[5]); lo.z = *reinterpret_cast<uint32_t *>(&h);
-      h = __floats2half2_rn(f[6], f[7]); lo.w = *reinterpret_cast<uint32_t *>(&h);
-      h = __floats2half2_rn(f[1], f[2]); hi.x = *reinterpret_cast<uint32_t *>(&h);
-      h = __floats2half2_rn(f[3], f[4]); hi.y = *reinterpret_cast<uint32_t *>(&h);
-      h = __floats2half2_rn(f[5], f[6]); hi.z = *reinterpret_cast<uint32_t *>(&h);
-      h = __floats2half2_rn(f[7], f[8]); hi.w = *reinterpret_cast<uint32_t *>(&h);
-      *reinterpret_cast<uint4 *>(dst) = lo;
-      *reinterpret_cast<uint4 *>(dst + 48) = hi;
     };
     // one thread issues the MMAs of element layer L (node planes L, L+1),
     // tile 0 first, with one commit per tile
@@ -493,19 +501,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mma_f16_elect(tcol + (uint32_t)(s * TC_N), a1 + off,
                       bdesc0 + (uint64_t)((2 * 6 * kBlockBytes) >> 4), 1);
       }
-      mma_commit_elect(&bars[4 + warp]);
+      mma_commit_elect(&bars[8 + warp]);
     };
 
-    // ---- segment prologue: planes Z0-1, Z0, Z0+1 ---------------------------
+    // ---- segment prologue: planes Z0-1 .. Z0+2 ----------------------------
+    // (a segment owns at least one plane, so planes up to Z0+1 = Lfirst+2 exist)
     const int Lfirst = Z0 - 1, Llast = Z1 - 1;
-    issue_plane(Lfirst);
-    issue_plane(Lfirst + 1);
-    issue_plane(Lfirst + 2);
-    bool ok = wait_plane(Lfirst);
-    ok = wait_plane(Lfirst + 1) && ok;
+    issue_plane(Lfirst, 0);
+    issue_plane(Lfirst + 1, 0);
+    issue_plane(Lfirst + 2, 0);
+    if (Lfirst + 3 <= Llast + 1) issue_plane(Lfirst + 3, 0);
+    bool ok = wait_plane(Lfirst, true);
+    ok = wait_plane(Lfirst + 1, true) && ok;
+    ok = wait_plane(Lfirst + 2, true) && ok;
     if (sync_abort(ok)) { aborted = true; break; }
-    digitise(Lfirst);
-    digitise(Lfirst + 1);
+    for (int t = tid; t < ntask; t += TC_THREADS) {
+      digitise_task(Lfirst, t);
+      digitise_task(Lfirst + 1, t);
+      digitise_task(Lfirst + 2, t);
+    }
     fence_async_smem();
     __syncthreads();
     issue_mma(Lfirst);
@@ -517,6 +531,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                  : -1;
     };
     int m_next = mat_at(Lfirst);
+    bool okp = true;  // plane waits of the previous layer's second phase
     for (int L = Lfirst; L <= Llast; ++L) {
       const int m = m_next;
       m_next = mat_at(L + 1);
@@ -529,15 +544,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int c = 0; c < 3; ++c) uprev[c] = d.U_prev[c * d.comp + nidx];
       }
 
-      // (a) digitise plane L+2 while MMA(L) runs; prefetch plane L+3
-      bool okp = true;
-      if (L + 2 <= Llast + 1) okp = wait_plane(L + 2);
-      if (sync_abort(okp)) { aborted = true; break; }
-      if (L + 2 <= Llast + 1) digitise(L + 2);
-      if (L + 3 <= Llast + 1) issue_plane(L + 3);
-
       // (b) wait for this warp's tile of MMA(L)
-      const bool okm = mbar_wait(&bars[4 + tile], mma_phase);
+      const bool okm = mbar_wait(&bars[8 + tile], mma_phase);
       mma_phase ^= 1u;
       if (!okm) atomicExch(&misc[1], 1u);
       tc_fence_after();
@@ -549,58 +557,61 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t tbase =
           tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * kTileCols);
       int64_t own[3] = {0, 0, 0};  // this half's (dy = 1) corner sums
-      int64_t *yb_half = ybuf + half * (TC_EX * TC_EX * 3);
+      int64_t *yb_half = ybuf + (2 * half + (L & 1)) * (TC_EX * TC_EX * 3);
 #pragma unroll
       for (int gg = 0; gg < 2; ++gg) {
         const int g = 2 * half + gg;
         // this group's 12 outputs (dx, part, component) are 12 contiguous
-        // columns per stage; load all stages (x8 + x4 each), wait once
-        uint32_t w[TC_MAX_STAGES][12];
+        // columns per stage; each dx half (P0 P1 P2 Q0 Q1 Q2) is loaded for all
+        // stages (x4 + x2, each aligned to its size) and reduced before the next
         const int c0 = 24 * half + 12 * gg;  // 0, 12, 24, 36
+        const int dy = g & 1, dz = g >> 1;
+        int64_t f0[3], f1[3];
 #pragma unroll
-        for (int s = 0; s < TC_MAX_STAGES; ++s) {
-          if constexpr (s_lo > 0) {
-            if (s < s_lo) {  // dropped low digit: a zero partial product
+        for (int dx = 0; dx < 2; ++dx) {
+          uint32_t w[TC_MAX_STAGES][6];
 #pragma unroll
-              for (int i = 0; i < 12; ++i) w[s][i] = TC_MAGIC_BITS;
-              continue;
+          for (int s = 0; s < TC_MAX_STAGES; ++s) {
+            if constexpr (s_lo > 0) {
+              if (s < s_lo) {  // dropped low digit: a zero partial product
+#pragma unroll
+                for (int i = 0; i < 6; ++i) w[s][i] = TC_MAGIC_BITS;
+                continue;
+              }
+            }
+            const uint32_t ta = tbase + (uint32_t)(s * TC_N + c0 + 6 * dx);
+            if (dx == 0) {  // column c0 = 0 mod 4
+              tmem_ld4(ta, w[s][0], w[s][1], w[s][2], w[s][3]);
+              tmem_ld2(ta + 4, w[s][4], w[s][5]);
+            } else {        // column c0 + 6 = 2 mod 4
+              tmem_ld2(ta, w[s][0], w[s][1]);
+              tmem_ld4(ta + 2, w[s][2], w[s][3], w[s][4], w[s][5]);
             }
           }
-          const uint32_t ta = tbase + (uint32_t)(s * TC_N + c0);
-          if (gg == 0) {  // c0 = 0 or 24: x8 at c0, x4 at c0 + 8 (each aligned to its size)
-            tmem_ld8(ta, w[s]);
-            tmem_ld4(ta + 8, w[s][8], w[s][9], w[s][10], w[s][11]);
-          } else {        // c0 = 12 or 36: x4 at c0, x8 at c0 + 4
-            tmem_ld4(ta, w[s][0], w[s][1], w[s][2], w[s][3]);
-            tmem_ld8(ta + 4, w[s] + 4);
-          }
-        }
-        tmem_wait_ld();
-        int64_t pq[12];
+          tmem_wait_ld();
+          int64_t pq[6];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) pq[i] = recombine5(w[0][i], w[1][i], w[2][i], w[3][i], w[4][i]);
-        const int dy = g & 1, dz = g >> 1;
-        if constexpr (MODE == TC_MODE_PARTIALS) {
-          if (elem_xy && L >= 0 && L < d.nz) {
-            const int64_t e = (int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L);
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
+          for (int i = 0; i < 6; ++i) pq[i] = recombine5(w[0][i], w[1][i], w[2][i], w[3][i], w[4][i]);
+          if constexpr (MODE == TC_MODE_PARTIALS) {
+            if (elem_xy && L >= 0 && L < d.nz) {
+              const int64_t e = (int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L);
               const int a = dx + 2 * dy + 4 * dz;
 #pragma unroll
               for (int c = 0; c < 3; ++c) {
-                d.partials_out[e * 48 + 3 * a + c] = pq[6 * dx + c];
-                d.partials_out[e * 48 + 24 + 3 * a + c] = pq[6 * dx + 3 + c];
+                d.partials_out[e * 48 + 3 * a + c] = pq[c];
+                d.partials_out[e * 48 + 24 + 3 * a + c] = pq[3 + c];
               }
             }
-          }
-        } else {
-          // material: t = (P A + Q B) / 2^63 in the mesh-wide unit
-          int64_t f0[3], f1[3];
+          } else {
+            // material: t = (P A + Q B) / 2^63 in the mesh-wide unit
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            f0[c] = mul2_hi63(pq[c], pq[3 + c], A1, A0, B1, B0);
-            f1[c] = mul2_hi63(pq[6 + c], pq[9 + c], A1, A0, B1, B0);
+            for (int c = 0; c < 3; ++c) {
+              const int64_t t = mul2_hi63(pq[c], pq[3 + c], A1, A0, B1, B0);
+              if (dx == 0) f0[c] = t; else f1[c] = t;
+            }
           }
+        }
+        if constexpr (MODE != TC_MODE_PARTIALS) {
           // x reduction: node (ei+1) gets dx=1 of element ei and dx=0 of ei+1
           int64_t v[3];
 #pragma unroll
@@ -621,8 +632,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // (d) TMEM reads done; digit writes visible to the tensor core; MMA(L+1)
       tc_fence_before();
       fence_async_smem();
-      if (sync_abort(true)) { aborted = true; break; }
+      if (sync_abort(okp)) { aborted = true; break; }
       if (L + 1 <= Llast) issue_mma(L + 1);
+
+      // second phase: half 1 digitises plane L+3 (read by MMA(L+2)) and
+      // prefetches plane L+4 while half 0 updates plane L.  Every thread keeps
+      // the U-slot phase bookkeeping; only half 1 waits.
+      okp = true;
+      if (L + 3 <= Llast + 1) okp = wait_plane(L + 3, half == 1);
+      if (L + 4 <= Llast + 1) issue_plane(L + 4, TC_THREADS / 2);
+      if (half == 1 && L + 3 <= Llast + 1)
+        for (int t = tid - TC_THREADS / 2; t < ntask; t += TC_THREADS / 2) digitise_task(L + 3, t);
       if constexpr (MODE == TC_MODE_PARTIALS) continue;
 
       // (e) y reduction from the shared buffer.  Half 1 holds the forces of
@@ -650,7 +670,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int c = 0; c < 3; ++c) d.S_out[c * d.comp + nidx] = S[c];
         } else if (MODE == TC_MODE_STEP) {
-          const int64_t *ucur = uslot + (L & 3) * (kUSlotStride / 8);
+          // plane L's slot completed its phase before half 1 digitised it; the
+          // wait returns at once and orders the TMA data before these reads
+          if (!mbar_wait(&bars[L & 7], ((uphase >> (L & 7)) & 1u) ^ 1u)) atomicExch(&misc[1], 1u);
+          const int64_t *ucur = uslot + (L & 7) * (kUSlotStride / 8);
           const bool is_src = (nidx == d.src_node);
           int64_t unew[3], uold[3];
 #pragma unroll
