@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--stages", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--trace-steps", type=int, default=2000,
+                    help="length of the untimed TC vs FP64 path trace comparison "
+                         "(capped by the workload's own length)")
     ap.add_argument("--workload", default="config2",
                     choices=["config2", "config3", "config4", "paper_rebar"],
                     help="config2 (default) is the benchmark model; the others are reported "
@@ -286,7 +289,7 @@ def run_ours(args):
         cfg["speedup_vs_fp64_path"] = (value / world) / f_value
         # the workload's full length (at most 2,000 steps) on both paths from
         # rest (untimed)
-        nt = min(int(mesh["nsteps"]), 2000)
+        nt = min(int(mesh["nsteps"]), args.trace_steps)
         trs = []
         for path in (vfe.VFE_PATH_TC, vfe.VFE_PATH_FP64):
             mp = vfe.Mesh(mesh, path=path, stages=args.stages, stream=stream.cuda_stream,

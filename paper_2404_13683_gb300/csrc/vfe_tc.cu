@@ -171,17 +171,33 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t &a, uint32_t &
                : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t &a, uint32_t &b) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
-               : "=r"(a), "=r"(b)
-               : "r"(taddr));
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
                  "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
+}
+
+// Load 12 consecutive columns (x8 at c, x4 at c + 8 when c = 0 mod 8, else x4
+// at c and x8 at c + 4) of this warp's lanes.
+__device__ __forceinline__ void tmem_ld12(uint32_t taddr, bool first8, uint32_t *r) {
+  if (first8) {
+    tmem_ld8(taddr, r);
+    tmem_ld4(taddr + 8, r[8], r[9], r[10], r[11]);
+  } else {
+    tmem_ld4(taddr, r[0], r[1], r[2], r[3]);
+    tmem_ld8(taddr + 4, r + 4);
+  }
+}
+
+// Wait for this thread's TMEM loads; the loaded registers pass through the
+// statement so no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld12(uint32_t *r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11])
+               :
+               : "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_ld() {
@@ -214,33 +230,28 @@ __device__ __forceinline__ float int_to_f32_exact(int d) {
 // ---------------------------------------------------------------------------
 // Epilogue arithmetic.
 // ---------------------------------------------------------------------------
-// Exact P = sum_s 2^(11 s) D_s from the five magic-biased accumulator words
-// w_s = 0x4B400000 + D_s of one output, as one mad.wide chain: the biased
-// words are combined unsigned and the bias removed once (mod 2^64 arithmetic
-// is exact because the true P fits in int64).  |q| < 2^51 keeps |D_4| < 2^18,
-// so (w_4 - bias) * 4096 fits the high word.
-__device__ __forceinline__ int64_t recombine5(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
-                                              uint32_t w4) {
-  constexpr uint64_t kBias = (uint64_t)TC_MAGIC_BITS * (1ull + 2048ull + 4194304ull + 8589934592ull);
-  uint64_t p;
-  asm("{\n"
-      " .reg .u64 t;\n"
-      " .reg .u32 lo, hi, d4;\n"
-      " mov.b64 t, {%1, 0};\n"
-      " mad.wide.u32 t, %2, 2048, t;\n"
-      " mad.wide.u32 t, %3, 4194304, t;\n"
-      " mov.b64 {lo, hi}, t;\n"
-      " mad.lo.u32 hi, %4, 2, hi;\n"
-      " sub.u32 d4, %5, %6;\n"
-      " mad.lo.u32 hi, d4, 4096, hi;\n"
-      " sub.cc.u32 lo, lo, %7;\n"
-      " subc.u32 hi, hi, %8;\n"
-      " mov.b64 %0, {lo, hi};\n"
-      "}\n"
-      : "=l"(p)
-      : "r"(w0), "r"(w1), "r"(w2), "r"(w3), "r"(w4), "r"((uint32_t)TC_MAGIC_BITS),
-        "r"((uint32_t)kBias), "r"((uint32_t)(kBias >> 32)));
-  return (int64_t)p;
+// One stage of the exact recombination P = sum_s 2^(11 s) D_s of the
+// magic-biased accumulator words w_s = 0x4B400000 + D_s, Horner order over the
+// stages; the biases of all five words are removed at the end by
+// recomb_finish (mod 2^64 arithmetic is exact because P fits in int64).
+template <int S>
+__device__ __forceinline__ void recomb_stage(uint64_t &t, uint32_t w) {
+  if constexpr (S == 0) {
+    t = (uint64_t)w;
+  } else if constexpr (S == 1) {
+    asm("mad.wide.u32 %0, %1, 2048, %0;" : "+l"(t) : "r"(w));
+  } else if constexpr (S == 2) {
+    asm("mad.wide.u32 %0, %1, 4194304, %0;" : "+l"(t) : "r"(w));
+  } else if constexpr (S == 3) {
+    t += (uint64_t)(w << 1) << 32;
+  } else {
+    t += (uint64_t)(w << 12) << 32;
+  }
+}
+__device__ __forceinline__ int64_t recomb_finish(uint64_t t) {
+  constexpr uint64_t kBias = (uint64_t)TC_MAGIC_BITS *
+                             (1ull + 2048ull + 4194304ull + 8589934592ull + 17592186044416ull);
+  return (int64_t)(t - kBias);
 }
 
 // floor((P A + Q B) / 2^63) within 4 units, for the material multipliers
@@ -269,6 +280,28 @@ __device__ __forceinline__ int64_t mul2_hi63(int64_t P, int64_t Q, int A1, int A
       "}\n"
       : "=l"(r)
       : "l"(P), "l"(Q), "r"(A1), "r"(A0), "r"(B1), "r"(B0));
+  return r;
+}
+
+// floor(P C / 2^63) within 2 units for 0 <= C = C1 2^31 + C0 < 2^62 and
+// |P| < 2^63: the same limb products as mul2_hi63 for one term.
+__device__ __forceinline__ int64_t mul_hi63(int64_t P, int C1, int C0) {
+  int64_t r;
+  asm("{\n"
+      " .reg .u32 p0, p1;\n"
+      " .reg .u64 lo, res;\n"
+      " .reg .s64 mid;\n"
+      " mov.b64 {p0, p1}, %1;\n"
+      " mul.wide.u32 lo, p0, %2;\n"
+      " shr.u64 lo, lo, 1;\n"
+      " mul.wide.s32 mid, p1, %3;\n"
+      " add.s64 mid, mid, lo;\n"
+      " shr.s64 mid, mid, 31;\n"
+      " mul.wide.s32 res, p1, %2;\n"
+      " add.s64 %0, res, mid;\n"
+      "}\n"
+      : "=l"(r)
+      : "l"(P), "r"(C1), "r"(C0));
   return r;
 }
 
@@ -317,8 +350,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (tid == 0) {
     misc[1] = 0;
     for (int i = 0; i < kUSlots; ++i) mbar_init(&bars[i], 1);
-    mbar_init(&bars[8], 1);
-    mbar_init(&bars[9], 1);
+    mbar_init(&bars[8], 2);
+    mbar_init(&bars[9], 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -486,22 +519,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint64_t adesc0 = make_sdesc(smem_u32(digits), 2 * kBlockBytes, kBlockBytes);
     const uint64_t bdesc0 = make_sdesc(smem_u32(bop), 6 * kBlockBytes, kBlockBytes);
     // warp t issues the MMAs of tile t (both warps are converged here)
+    // warps 8-11 (second half) issue: tile (w & 1), stages split in two parts;
+    // each commits its own MMAs to the tile's mbarrier (two arrivals)
     auto issue_mma = [&](int L) {
-      if (warp >= 2) return;
+      const int iw = warp - TC_THREADS / 64;
+      if (iw < 0 || iw >= 4) return;
+      const int mt = iw & 1, part = iw >> 1;
       tc_fence_after();
       const int sl0 = ((L % kDigitSlots) + kDigitSlots) % kDigitSlots;
       const int sl1 = sl0 == kDigitSlots - 1 ? 0 : sl0 + 1;
-      const uint64_t a0 = adesc0 + (uint64_t)((sl0 * kDigitSlotBytes + 16 * warp * kBlockBytes) >> 4);
-      const uint64_t a1 = adesc0 + (uint64_t)((sl1 * kDigitSlotBytes + 16 * warp * kBlockBytes) >> 4);
-      const uint32_t tcol = (uint32_t)(warp * kTileCols);
+      const uint64_t a0 = adesc0 + (uint64_t)((sl0 * kDigitSlotBytes + 16 * mt * kBlockBytes) >> 4);
+      const uint64_t a1 = adesc0 + (uint64_t)((sl1 * kDigitSlotBytes + 16 * mt * kBlockBytes) >> 4);
+      const uint32_t tcol = (uint32_t)(mt * kTileCols);
+      constexpr int s_mid = s_lo + (STAGES + 1) / 2;
 #pragma unroll
       for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
+        if ((s < s_mid) != (part == 0)) continue;
         const uint64_t off = (uint64_t)((s * kStageBytes) >> 4);
         mma_f16_elect(tcol + (uint32_t)(s * TC_N), a0 + off, bdesc0, 0);
         mma_f16_elect(tcol + (uint32_t)(s * TC_N), a1 + off,
                       bdesc0 + (uint64_t)((2 * 6 * kBlockBytes) >> 4), 1);
       }
-      mma_commit_elect(&bars[8 + warp]);
+      mma_commit_elect(&bars[8 + mt]);
     };
 
     // ---- segment prologue: planes Z0-1 .. Z0+2 ----------------------------
@@ -562,53 +601,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int gg = 0; gg < 2; ++gg) {
         const int g = 2 * half + gg;
         // this group's 12 outputs (dx, part, component) are 12 contiguous
-        // columns per stage; each dx half (P0 P1 P2 Q0 Q1 Q2) is loaded for all
-        // stages (x4 + x2, each aligned to its size) and reduced before the next
+        // columns per stage, recombined in Horner order while the next stage's
+        // words load (two buffers of 12 words)
         const int c0 = 24 * half + 12 * gg;  // 0, 12, 24, 36
+        const bool first8 = (c0 & 7) == 0;
         const int dy = g & 1, dz = g >> 1;
-        int64_t f0[3], f1[3];
+        uint64_t acc[12];
+        uint32_t wa[12], wb[12];
+        static_assert(STAGES >= 1 && STAGES <= TC_MAX_STAGES, "stages");
+        if constexpr (s_lo == 0) {  // otherwise the loop loads stage s_lo first
+          tmem_ld12(tbase + (uint32_t)(s_lo * TC_N + c0), first8, wa);
+          tmem_wait_ld12(wa);
+        }
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          uint32_t w[TC_MAX_STAGES][6];
+        for (int s = 0; s < TC_MAX_STAGES; ++s) {
+          // the words of stage s are in wa (s - s_lo even) or wb (odd);
+          // dropped low digits contribute magic-only words
+          uint32_t *cur = ((s - s_lo) & 1) ? wb : wa;
+          uint32_t *nxt = ((s - s_lo) & 1) ? wa : wb;
+          if (s + 1 < TC_MAX_STAGES && s + 1 >= s_lo)
+            tmem_ld12(tbase + (uint32_t)((s + 1) * TC_N + c0), first8, nxt);
 #pragma unroll
-          for (int s = 0; s < TC_MAX_STAGES; ++s) {
-            if constexpr (s_lo > 0) {
-              if (s < s_lo) {  // dropped low digit: a zero partial product
-#pragma unroll
-                for (int i = 0; i < 6; ++i) w[s][i] = TC_MAGIC_BITS;
-                continue;
-              }
-            }
-            const uint32_t ta = tbase + (uint32_t)(s * TC_N + c0 + 6 * dx);
-            if (dx == 0) {  // column c0 = 0 mod 4
-              tmem_ld4(ta, w[s][0], w[s][1], w[s][2], w[s][3]);
-              tmem_ld2(ta + 4, w[s][4], w[s][5]);
-            } else {        // column c0 + 6 = 2 mod 4
-              tmem_ld2(ta, w[s][0], w[s][1]);
-              tmem_ld4(ta + 2, w[s][2], w[s][3], w[s][4], w[s][5]);
-            }
+          for (int i = 0; i < 12; ++i) {
+            const uint32_t w = s < s_lo ? (uint32_t)TC_MAGIC_BITS : cur[i];
+            if (s == 0) recomb_stage<0>(acc[i], w);
+            else if (s == 1) recomb_stage<1>(acc[i], w);
+            else if (s == 2) recomb_stage<2>(acc[i], w);
+            else if (s == 3) recomb_stage<3>(acc[i], w);
+            else recomb_stage<4>(acc[i], w);
           }
-          tmem_wait_ld();
-          int64_t pq[6];
+          if (s + 1 < TC_MAX_STAGES && s + 1 >= s_lo) tmem_wait_ld12(nxt);
+        }
+        int64_t f0[3], f1[3];
+        if constexpr (MODE == TC_MODE_PARTIALS) {
+          if (elem_xy && L >= 0 && L < d.nz) {
+            const int64_t e = (int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L);
 #pragma unroll
-          for (int i = 0; i < 6; ++i) pq[i] = recombine5(w[0][i], w[1][i], w[2][i], w[3][i], w[4][i]);
-          if constexpr (MODE == TC_MODE_PARTIALS) {
-            if (elem_xy && L >= 0 && L < d.nz) {
-              const int64_t e = (int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L);
+            for (int dx = 0; dx < 2; ++dx) {
               const int a = dx + 2 * dy + 4 * dz;
 #pragma unroll
               for (int c = 0; c < 3; ++c) {
-                d.partials_out[e * 48 + 3 * a + c] = pq[c];
-                d.partials_out[e * 48 + 24 + 3 * a + c] = pq[3 + c];
+                d.partials_out[e * 48 + 3 * a + c] = recomb_finish(acc[6 * dx + c]);
+                d.partials_out[e * 48 + 24 + 3 * a + c] = recomb_finish(acc[6 * dx + 3 + c]);
               }
             }
-          } else {
-            // material: t = (P A + Q B) / 2^63 in the mesh-wide unit
+          }
+        } else {
+          // material: t = (P A + Q B) / 2^63 in the mesh-wide unit
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              const int64_t t = mul2_hi63(pq[c], pq[3 + c], A1, A0, B1, B0);
-              if (dx == 0) f0[c] = t; else f1[c] = t;
-            }
+          for (int c = 0; c < 3; ++c) {
+            f0[c] = mul2_hi63(recomb_finish(acc[c]), recomb_finish(acc[3 + c]), A1, A0, B1, B0);
+            f1[c] = mul2_hi63(recomb_finish(acc[6 + c]), recomb_finish(acc[9 + c]), A1, A0, B1, B0);
           }
         }
         if constexpr (MODE != TC_MODE_PARTIALS) {
@@ -675,19 +718,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (!mbar_wait(&bars[L & 7], ((uphase >> (L & 7)) & 1u) ^ 1u)) atomicExch(&misc[1], 1u);
           const int64_t *ucur = uslot + (L & 7) * (kUSlotStride / 8);
           const bool is_src = (nidx == d.src_node);
+          // du = round(S C / 2^R): for R >= 63 (the usual case: C < 2^62 and
+          // |S| < 2^63) from the high product floor(S C / 2^63), within a few
+          // units of the 59-bit state; otherwise exactly in 128 bits
+          const int C1 = (int)(cn >> 31), C0 = (int)(cn & 0x7FFFFFFF);
+          const bool rescaled = (P.rs | P.rs_prev) != 0;
           int64_t unew[3], uold[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const int64_t u0 =
-                shr_round(ucur[(c * TC_NODES + ej + 1) * TC_BOXX + ei + 1 + xo], P.rs);
-            const int64_t um = shr_round(uprev[c], P.rs + P.rs_prev);
-            const __int128 prod = (__int128)S[c] * (__int128)cn;
+            int64_t u0 = ucur[(c * TC_NODES + ej + 1) * TC_BOXX + ei + 1 + xo];
+            int64_t um = uprev[c];
+            if (rescaled) {
+              u0 = shr_round(u0, P.rs);
+              um = shr_round(um, P.rs + P.rs_prev);
+            }
             int64_t du;
-            if (Rseg > 0) {
-              const int R = min(Rseg, 126);
-              du = (int64_t)((prod + ((__int128)1 << (R - 1))) >> R);
-            } else {  // the state is being scaled up: exact left shift
-              du = (int64_t)(prod << min(-Rseg, 63));
+            if (Rseg >= 63) {
+              const int64_t H = mul_hi63(S[c], C1, C0);
+              const int sh = Rseg - 63;
+              du = sh == 0 ? H : (sh > 62 ? 0 : (H + ((int64_t)1 << (sh - 1))) >> sh);
+            } else {
+              const __int128 prod = (__int128)S[c] * (__int128)cn;
+              if (Rseg > 0) {
+                du = (int64_t)((prod + ((__int128)1 << (Rseg - 1))) >> Rseg);
+              } else {  // the state is being scaled up: exact left shift
+                du = (int64_t)(prod << min(-Rseg, 63));
+              }
             }
             int64_t un = 2 * u0 - um - du;
             if (is_src) un += P.dU_src[c];
