@@ -157,9 +157,9 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def profiled_counters():
+    """DRAM bytes and warp instructions per launch from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
     try:
         with open(PROFILE_TXT) as f:
             text = f.read()
@@ -175,9 +175,15 @@ def profiled_traffic():
     if vals.get("kernel_source_sha256_16") != sha:
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        return {"dram_bytes": float(vals["dram_bytes_per_launch"]),
+                "warp_instructions": float(vals["smsp__inst_executed.sum"].split()[0])}
+    except (KeyError, ValueError, IndexError):
         return None
+
+
+# warp-instruction issue rate of a GB300: 152 SMs x 4 schedulers, one warp
+# instruction per scheduler per cycle, at the 2,070 MHz maximum SM clock
+ISSUE_PEAK_WARP_INST_PER_S = 152 * 4 * 2.070e9
 
 
 # --------------------------------------------------------------------------
@@ -306,10 +312,19 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     abytes = algorithmic_bytes_per_step(mesh)
     achieved = abytes / (ms_step * 1e-3) / 1e9
+    prof = profiled_counters() if args.workload == "config2" else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
-            "frac": achieved / float(peaks["hbm_gbs"]), "traffic": profiled_traffic(),
+            "frac": achieved / float(peaks["hbm_gbs"]),
+            "traffic": prof["dram_bytes"] if prof else None,
             "algorithmic_bytes_per_launch": abytes, "peak_source": peak_src,
             "kernel": "tc_step_kernel (duration includes the one-thread prologue launch)"}
+    if prof:
+        # the kernel is limited by instruction issue, not HBM: the same launch
+        # against the GPU's warp-instruction issue rate
+        ach_i = prof["warp_instructions"] / (ms_step * 1e-3)
+        roof["issue"] = {"achieved": ach_i, "peak": ISSUE_PEAK_WARP_INST_PER_S,
+                         "unit": "warp instructions/s", "frac": ach_i / ISSUE_PEAK_WARP_INST_PER_S,
+                         "warp_instructions_per_launch": prof["warp_instructions"]}
 
     # --- the CPU oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
