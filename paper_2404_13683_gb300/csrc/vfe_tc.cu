@@ -254,29 +254,33 @@ __device__ __forceinline__ int64_t recomb_finish(uint64_t t) {
   return (int64_t)(t - kBias);
 }
 
-// floor((P A + Q B) / 2^63) within 4 units, for the material multipliers
-// A = A1 2^31 + A0, B = B1 2^31 + B0 (0 <= A0, B0 < 2^31; 0 <= A1, B1 < 2^30)
-// and |P|, |Q| < 2^61:  P A / 2^63 = P1 A1 + (P1 A0 + P0 A1 / 2) / 2^31 + ...
-// with P = P1 2^32 + P0; the P0 A0 term is dropped.
+// floor((P A + Q B) / 2^63) within 4 units, for any int64 P, Q and the
+// material multipliers A = A1 2^31 + A0, B = B1 2^31 + B0 (0 <= A0, B0 < 2^31;
+// 0 <= A1, B1 < 2^30).  With P = p1 2^32 + p0 (p1 signed, p0 unsigned):
+//   P A / 2^63 = p1 A1 + p1 A0 / 2^31 + p0 A1 / 2^32 + p0 A0 / 2^63,
+// and likewise for Q B.  The three leading terms of both products are summed
+// as p1 A1 + q1 B1, floor((p1 A0 + q1 B0) / 2^31) (|.| < 2^63) and the high
+// word of p0 A1 + q0 B1 (< 2^63); the last terms (< 2 together) are dropped.
 __device__ __forceinline__ int64_t mul2_hi63(int64_t P, int64_t Q, int A1, int A0, int B1,
                                              int B0) {
   int64_t r;
   asm("{\n"
-      " .reg .u32 p0, p1, q0, q1;\n"
-      " .reg .u64 lo, res;\n"
-      " .reg .s64 mid;\n"
+      " .reg .u32 p0, p1, q0, q1, l0, l1;\n"
+      " .reg .u64 lo, t3;\n"
+      " .reg .s64 mid, res;\n"
       " mov.b64 {p0, p1}, %1;\n"
       " mov.b64 {q0, q1}, %2;\n"
       " mul.wide.u32 lo, p0, %3;\n"
       " mad.wide.u32 lo, q0, %5, lo;\n"
-      " shr.u64 lo, lo, 1;\n"
+      " mov.b64 {l0, l1}, lo;\n"
+      " cvt.u64.u32 t3, l1;\n"
       " mul.wide.s32 mid, p1, %4;\n"
       " mad.wide.s32 mid, q1, %6, mid;\n"
-      " add.s64 mid, mid, lo;\n"
       " shr.s64 mid, mid, 31;\n"
       " mul.wide.s32 res, p1, %3;\n"
       " mad.wide.s32 res, q1, %5, res;\n"
-      " add.s64 %0, res, mid;\n"
+      " add.s64 res, res, mid;\n"
+      " add.s64 %0, res, t3;\n"
       "}\n"
       : "=l"(r)
       : "l"(P), "l"(Q), "r"(A1), "r"(A0), "r"(B1), "r"(B0));
@@ -660,7 +664,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             const int64_t nb = __shfl_down_sync(0xffffffffu, f0[c], 1);
-            v[c] = f1[c] + (ei < TC_EX - 1 ? nb : 0);
+            v[c] = f1[c] + nb;  // lane ei = 15 reads the next row: its node is not owned
           }
           if (dy == 0) {
             int64_t *yb = yb_half + (ej * TC_EX + ei) * 3;
