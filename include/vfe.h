@@ -99,6 +99,20 @@ int vfe_internal_force(vfe_mesh *mesh, const double *u, double *f);
  * device errors surface at the next synchronising call. */
 int vfe_step(vfe_mesh *mesh, int n);
 
+/* Advance n >= 0 steps like vfe_step, with the point force at the source
+ * node given by the caller instead of the wavelet: step k of these n uses
+ * F = force[k][0..2] (newtons, FP64 host array [n][3]) in the update of
+ * Eq. eqtimehistory, as the experiment of Section 3 drives its model through
+ * a prescribed force at one node.  Needs a prior vfe_set_source (its node is
+ * used; its wavelet parameters are not); a force at a fixed or massless node
+ * is ignored.  Later vfe_step calls use the wavelet again.  The rows are
+ * copied to the device on the mesh's stream: a pageable array is read before
+ * the call returns, a page-locked one must stay unchanged until the next
+ * synchronising call.  Asynchronous like vfe_step.  Errors: VFE_EINVAL (NULL
+ * force, n < 0, a non-finite value), VFE_ESTATE (no source set), VFE_ENOMEM
+ * (growing the device copy of the rows), VFE_ECUDA. */
+int vfe_step_forced(vfe_mesh *mesh, int n, const double *force);
+
 /* Block until queued work is done; reports device-side timeouts. */
 int vfe_synchronize(vfe_mesh *mesh);
 

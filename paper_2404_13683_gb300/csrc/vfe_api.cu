@@ -141,6 +141,7 @@ struct vfe_mesh {
   std::vector<int32_t> rec_ijk;
 
   bool has_src = false;
+  bool src_set = false;  // vfe_set_source was called
   int64_t src_node = -1;
   double src_dir[3] = {0, 0, 0}, f0 = 0, t0 = 0, amp = 0;
   int cur = 0;  // which state buffer holds u^n
@@ -178,6 +179,9 @@ struct vfe_mesh {
   bool graph_valid[2] = {false, false};
   int64_t gen = 0;  // bumped whenever kernel arguments change (batches rebuild)
   double *d_inj = nullptr;  // injection array [rows][n_rec][3] (adjoint source)
+  double *d_force = nullptr;  // explicit force rows of vfe_step_forced [k][3], then one
+                              // int64 -1 (copied to the "first step" slot to end a series)
+  int64_t force_cap = 0;      // rows d_force holds
   std::vector<double> table;  // the caller's {Vp, Vs, rho} rows
 };
 
@@ -240,8 +244,11 @@ static int enqueue_step(vfe_mesh *m, int cur) {
   src.f0 = m->f0;
   src.t0 = m->t0;
   for (int c = 0; c < 3; ++c) src.dir[c] = m->src_dir[c];
+  src.force = m->d_force;
+  src.force_rows = m->force_cap;
   if (m->opt.path == VFE_PATH_TC) {
     src.amp_scale = m->amp * m->src_scale;
+    src.force_scale = m->src_scale;
     CUDA_TRY(tc_launch_prologue_ex(m->stream, m->d_tcparams, m->d_tcpersist, src, m->d_or,
                                    m->tiles_x * m->tiles_y, m->has_src ? 1 : 0, trace_on,
                                    m->d_status, m->d_inj, 3 * m->n_rec));
@@ -249,8 +256,9 @@ static int enqueue_step(vfe_mesh *m, int cur) {
     CUDA_TRY(tc_launch_step(m->stream, d, &m->tmap[cur], TC_MODE_STEP));
   } else {
     src.amp_scale = m->amp;
+    src.force_scale = 1.0;
     CUDA_TRY(f64_launch_prologue(m->stream, m->d_f64params, m->d_f64persist, src,
-                                 m->has_src ? 1 : 0, trace_on));
+                                 m->has_src ? 1 : 0, trace_on, m->d_status));
     F64Device d = f64_device(m, cur);
     CUDA_TRY(f64_launch_step(m->stream, d, m->d_f64params, 0));
   }
@@ -282,6 +290,7 @@ static int check_status(vfe_mesh *m) {
   CUDA_TRY(cudaMemcpy(&st, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st & 1) return fail(VFE_ETIMEOUT, "a device-side wait timed out (status %d)", st);
   if (st & 2) return fail(VFE_ETIMEOUT, "fixed-point shift out of range (status %d)", st);
+  if (st & 8) return fail(VFE_ESTATE, "a forced step ran past the supplied force rows (status %d)", st);
   return VFE_OK;
 }
 
@@ -312,7 +321,7 @@ int vfe_destroy(vfe_mesh *m) {
                   m->d_dt2m, m->d_K, m->d_recnodes, m->d_f64params, m->d_f64persist,
                   m->d_U[0], m->d_U[1], m->d_C, m->d_Bop, m->d_mats, m->d_recv,
                   m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist, m->d_segs,
-                  m->d_seg_off, m->d_inj};
+                  m->d_seg_off, m->d_inj, m->d_force};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -471,12 +480,12 @@ static int build_f64(vfe_mesh *m) {
   CUDA_TRY(cudaMalloc(&m->d_u[0], sizeof(double) * 3 * m->nn));
   CUDA_TRY(cudaMalloc(&m->d_u[1], sizeof(double) * 3 * m->nn));
   CUDA_TRY(cudaMalloc(&m->d_f64params, f64_params_bytes()));
-  CUDA_TRY(cudaMalloc(&m->d_f64persist, sizeof(int64_t) * 4));
+  CUDA_TRY(cudaMalloc(&m->d_f64persist, sizeof(int64_t) * 6));
   CUDA_TRY(cudaMemcpy(m->d_K, K.data(), sizeof(double) * K.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(m->d_dt2m, dt2m.data(), sizeof(double) * m->nn, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(m->d_u[0], 0, sizeof(double) * 3 * m->nn));
   CUDA_TRY(cudaMemset(m->d_u[1], 0, sizeof(double) * 3 * m->nn));
-  const int64_t f64persist[4] = {0, 0, -1, 0};
+  const int64_t f64persist[6] = {0, 0, -1, 0, -1, 0};
   CUDA_TRY(cudaMemcpy(m->d_f64persist, f64persist, sizeof(f64persist), cudaMemcpyHostToDevice));
   return VFE_OK;
 }
@@ -603,7 +612,7 @@ static int build_tc(vfe_mesh *m) {
   CUDA_TRY(cudaMemcpy(m->d_mats, mats.data(), sizeof(TcMaterial) * mats.size(),
                       cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(m->d_or, 0, sizeof(unsigned long long) * or_words));
-  int64_t persist[8] = {0, 0, 0, 0, (int64_t)(m->eC + m->e_ref), 0, -1, 0};
+  int64_t persist[8] = {0, 0, 0, 0, (int64_t)(m->eC + m->e_ref), 0, -1, -1};
   CUDA_TRY(cudaMemcpy(m->d_tcpersist, persist, sizeof(persist), cudaMemcpyHostToDevice));
   // TMA maps over the two state buffers: (x, y, z, component), int64, box 18x17x1x3
   EncodeTiledFn enc = encode_fn();
@@ -696,6 +705,7 @@ int vfe_set_source(vfe_mesh *m, int i, int j, int k, const double dir[3], double
   CUDA_TRY(cudaStreamSynchronize(m->stream));
   const int64_t n = node_id(m, i, j, k);
   m->has_src = !m->fixed[n];
+  m->src_set = true;
   m->src_node = n;
   for (int c = 0; c < 3; ++c) m->src_dir[c] = dir[c];
   m->f0 = f0_hz;
@@ -744,11 +754,8 @@ static int ensure_trace_capacity(vfe_mesh *m, int64_t rows) {
   return VFE_OK;
 }
 
-int vfe_step(vfe_mesh *m, int n) {
-  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
-  if (n < 0) return fail(VFE_EINVAL, "n must be >= 0");
-  if (n == 0) return VFE_OK;
-  cudaSetDevice(m->device);
+// queue n steps on the mesh's stream (n >= 1, device already current)
+static int run_steps(vfe_mesh *m, int n) {
   int rc = ensure_trace_capacity(m, m->trace_rows + n);
   if (rc != VFE_OK) return rc;
   // pairs of steps replay a captured two-step graph; the source term, scales
@@ -768,6 +775,51 @@ int vfe_step(vfe_mesh *m, int n) {
   m->steps += n;
   if (m->n_rec) m->trace_rows += n;
   return VFE_OK;
+}
+
+int vfe_step(vfe_mesh *m, int n) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  if (n < 0) return fail(VFE_EINVAL, "n must be >= 0");
+  if (n == 0) return VFE_OK;
+  cudaSetDevice(m->device);
+  return run_steps(m, n);
+}
+
+int vfe_step_forced(vfe_mesh *m, int n, const double *force) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  if (n < 0) return fail(VFE_EINVAL, "n must be >= 0");
+  if (n == 0) return VFE_OK;
+  if (!force) return fail(VFE_EINVAL, "force is NULL");
+  if (!m->src_set) return fail(VFE_ESTATE, "no source node: call vfe_set_source first");
+  for (int64_t k = 0; k < 3 * (int64_t)n; ++k)
+    if (!std::isfinite(force[k])) return fail(VFE_EINVAL, "force[%lld] is not finite", (long long)k);
+  cudaSetDevice(m->device);
+  if (n > m->force_cap) {  // the prologues capture the buffer's address: new graphs
+    CUDA_TRY(cudaStreamSynchronize(m->stream));
+    const int64_t cap = std::max<int64_t>(n, std::max<int64_t>(2 * m->force_cap, 64));
+    double *p = nullptr;
+    if (cudaMalloc(&p, sizeof(double) * (3 * cap + 1)) != cudaSuccess)
+      return fail(VFE_ENOMEM, "force buffer of %lld rows", (long long)cap);
+    const int64_t off = -1;
+    CUDA_TRY(cudaMemcpy(p + 3 * cap, &off, sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (m->d_force) cudaFree(m->d_force);
+    m->d_force = p;
+    m->force_cap = cap;
+    invalidate_graphs(m);
+  }
+  // the rows, then first step := the device's own step counter, the steps,
+  // and the series ended again, all in stream order and without host staging
+  CUDA_TRY(cudaMemcpyAsync(m->d_force, force, sizeof(double) * 3 * n, cudaMemcpyHostToDevice,
+                           m->stream));
+  const bool tc = m->opt.path == VFE_PATH_TC;
+  int64_t *pers = tc ? m->d_tcpersist : m->d_f64persist;
+  const int slot_first = tc ? 7 : 4, slot_step = tc ? 1 : 0;
+  CUDA_TRY(cudaMemcpyAsync(pers + slot_first, pers + slot_step, sizeof(int64_t),
+                           cudaMemcpyDeviceToDevice, m->stream));
+  const int rc = run_steps(m, n);
+  CUDA_TRY(cudaMemcpyAsync(pers + slot_first, m->d_force + 3 * m->force_cap, sizeof(int64_t),
+                           cudaMemcpyDeviceToDevice, m->stream));
+  return rc;
 }
 
 int vfe_synchronize(vfe_mesh *m) {
@@ -1430,7 +1482,7 @@ int64_t *persist_ptr(vfe_mesh *m) {
   return m->opt.path == VFE_PATH_TC ? m->d_tcpersist : m->d_f64persist;
 }
 
-int persist_len(const vfe_mesh *m) { return m->opt.path == VFE_PATH_TC ? 8 : 4; }
+int persist_len(const vfe_mesh *m) { return m->opt.path == VFE_PATH_TC ? 8 : 6; }
 
 size_t slot_words(const vfe_mesh *m) { return 3 * (1 + (size_t)m->tiles_x * m->tiles_y); }
 
@@ -1486,11 +1538,11 @@ int rewind_mesh(vfe_mesh *m) {
   CUDA_TRY(cudaMemset(state_buf(m, 0), 0, sb));
   CUDA_TRY(cudaMemset(state_buf(m, 1), 0, sb));
   if (m->opt.path == VFE_PATH_TC) {
-    const int64_t p[8] = {0, 0, 0, 0, (int64_t)(m->eC + m->e_ref), 0, -1, 0};
+    const int64_t p[8] = {0, 0, 0, 0, (int64_t)(m->eC + m->e_ref), 0, -1, -1};
     CUDA_TRY(cudaMemcpy(m->d_tcpersist, p, sizeof(p), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(m->d_or, 0, sizeof(unsigned long long) * slot_words(m)));
   } else {
-    const int64_t p[4] = {0, 0, -1, 0};
+    const int64_t p[6] = {0, 0, -1, 0, -1, 0};
     CUDA_TRY(cudaMemcpy(m->d_f64persist, p, sizeof(p), cudaMemcpyHostToDevice));
   }
   m->cur = 0;

@@ -17,20 +17,29 @@ struct F64StepParams {
 };
 
 // persist[0] = step, [1] = trace rows, [2] = first step of the injection
-// array (-1: none)
+// array (-1: none), [3] unused, [4] = first step of the explicit force series
+// (-1: none), [5] unused
 __global__ void f64_prologue_kernel(F64StepParams *p, int64_t *persist, TcSource sd, int have_src,
-                                    int trace_on) {
+                                    int trace_on, int *status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int64_t n = persist[0];
   F64StepParams q;
   q.step = n;
   q.trace_row = trace_on ? persist[1] : -1;
   q.inj_row = persist[2] >= 0 ? n - persist[2] : -1;
-  // F^n = amp ricker(n dt) dir
-  const double fv = have_src ? sd.amp_scale * ricker_wavelet((double)n * sd.dt, sd.f0, sd.t0) : 0.0;
-  q.src[0] = fv * sd.dir[0];
-  q.src[1] = fv * sd.dir[1];
-  q.src[2] = fv * sd.dir[2];
+  // F^n = amp ricker(n dt) dir, or the caller's row of an explicit force series
+  q.src[0] = q.src[1] = q.src[2] = 0.0;
+  if (have_src && persist[4] >= 0 && sd.force) {
+    const int64_t frow = n - persist[4];
+    if (frow >= 0 && frow < sd.force_rows) {
+      for (int c = 0; c < 3; ++c) q.src[c] = sd.force_scale * sd.force[3 * frow + c];
+    } else {
+      atomicOr(status, 8);  // a forced step beyond the supplied rows: no force
+    }
+  } else if (have_src) {
+    const double fv = sd.amp_scale * ricker_wavelet((double)n * sd.dt, sd.f0, sd.t0);
+    for (int c = 0; c < 3; ++c) q.src[c] = fv * sd.dir[c];
+  }
   *p = q;
   persist[0] = n + 1;
   if (trace_on) persist[1] += 1;
@@ -118,9 +127,9 @@ static cudaError_t f64_launch(cudaStream_t s, const F64Device &d, const F64StepP
 size_t f64_params_bytes() { return sizeof(F64StepParams); }
 
 cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,
-                                const TcSource &src, int have_src, int trace_on) {
+                                const TcSource &src, int have_src, int trace_on, int *status) {
   f64_prologue_kernel<<<1, 32, 0, s>>>(reinterpret_cast<F64StepParams *>(params), persist, src,
-                                       have_src, trace_on);
+                                       have_src, trace_on, status);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,9 @@ struct TcPrologueArgs {       // one mesh's inputs to the per-step prologue
   double dir[3];
   int ncols, have_src, trace_on, n_inj;  // n_inj: values per injection row (3 n_rec)
   const double *inj;                     // injection array (see TcDevice::inj)
+  const double *force;                   // explicit force rows [k][3] (see TcSource)
+  double force_scale;
+  int64_t force_rows;
 };
 
 // FP64 path ------------------------------------------------------------------
@@ -138,10 +141,16 @@ struct F64Device {
 // Ricker point source (Section 3 applies an impulse force in z):
 // F(t) = amp_scale * (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2) * dir,
 // evaluated by the per-step prologue at t = n dt.  amp_scale is amp on the
-// FP64 path and amp * dt^2 / m(source node) on the TC path.
+// FP64 path and amp * dt^2 / m(source node) on the TC path.  While an explicit
+// force series is active (persist slot "first step" >= 0), step n takes
+// F^n = force[n - first][0..2] instead (force holds force_rows rows), scaled by
+// force_scale (1 on the FP64 path, dt^2 / m(source node) on the TC path).
 struct TcSource {
   double amp_scale, dt, f0, t0;
   double dir[3];
+  const double *force;
+  double force_scale;
+  int64_t force_rows;
 };
 
 __device__ __forceinline__ double ricker_wavelet(double t, double f0, double t0) {
@@ -186,5 +195,5 @@ cudaError_t grad_g_accumulate(cudaStream_t s, int nx, int ny, int nz, const int3
 
 size_t f64_params_bytes();
 cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,
-                                const TcSource &src, int have_src, int trace_on);
+                                const TcSource &src, int have_src, int trace_on, int *status);
 cudaError_t f64_launch_step(cudaStream_t s, const F64Device &d, const void *params, int mode);

@@ -809,9 +809,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ---------------------------------------------------------------------------
 // per-step prologue: rescale decision, digit shift, source increment
 // ---------------------------------------------------------------------------
-// persist[0] = F of u^n, [1] = step, [2] = trace rows, [4] = eC + e_ref,
-// [5] = shift of the last step (u^{n-1} has F + [5]), [6] = first step of the
-// injection array (-1: none)
+// persist[0] = F of u^n, [1] = step, [2] = trace rows, [3] unused,
+// [4] = eC + e_ref, [5] = shift of the last step
+// (u^{n-1} has F + [5]), [6] = first step of the injection array (-1: none),
+// [7] = first step of the explicit force series (-1: none)
 // One mesh's prologue, run by a block (thread 0 does the scalar work).
 __device__ void prologue_body(const TcPrologueArgs &A) {
   int64_t *persist = A.persist;
@@ -831,13 +832,21 @@ __device__ void prologue_body(const TcPrologueArgs &A) {
   int bs = 0;
   bool bs_valid = false;
   if (A.have_src) {
-    // F^n = amp ricker(n dt) dir, scaled by dt^2 / m of the source node
-    const double fv = A.amp_scale * ricker_wavelet((double)n * A.dt, A.f0, A.t0);
-    double mx = 0.0;
-    for (int c = 0; c < 3; ++c) {
-      src[c] = fv * A.dir[c];
-      mx = fmax(mx, fabs(src[c]));
+    // F^n = amp ricker(n dt) dir, or the caller's row of an explicit force
+    // series, scaled by dt^2 / m of the source node
+    const int64_t frow = n - persist[7];
+    if (persist[7] >= 0 && A.force) {
+      if (frow >= 0 && frow < A.force_rows) {
+        for (int c = 0; c < 3; ++c) src[c] = A.force_scale * A.force[3 * frow + c];
+      } else {
+        atomicOr(A.status, 8);  // a forced step beyond the supplied rows: no force
+      }
+    } else {
+      const double fv = A.amp_scale * ricker_wavelet((double)n * A.dt, A.f0, A.t0);
+      for (int c = 0; c < 3; ++c) src[c] = fv * A.dir[c];
     }
+    double mx = 0.0;
+    for (int c = 0; c < 3; ++c) mx = fmax(mx, fabs(src[c]));
     if (mx > 0.0) {
       bs = ilogb(mx) + F_old + 1;
       bs_valid = true;
@@ -882,9 +891,6 @@ __device__ void prologue_body(const TcPrologueArgs &A) {
   if (A.trace_on) persist[2] += 1;
 }
 
-// persist[0] = F of u^n, [1] = step, [2] = trace rows, [4] = eC + e_ref,
-// [5] = shift of the last step (u^{n-1} has F + [5]), [6] = first step of the
-// injection array (-1: none)
 __global__ void tc_prologue_kernel(const TcPrologueArgs A) { prologue_body(A); }
 
 __global__ void tc_batch_prologue_kernel(const TcPrologueArgs *args) {
@@ -912,6 +918,9 @@ cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t 
   A.trace_on = trace_on;
   A.n_inj = n_inj;
   A.inj = inj;
+  A.force = src.force;
+  A.force_scale = src.force_scale;
+  A.force_rows = src.force_rows;
   tc_prologue_kernel<<<1, 256, 0, s>>>(A);
   return cudaGetLastError();
 }

@@ -34,7 +34,7 @@ EXPORTS = (
     "vfe_get_state", "vfe_set_state", "vfe_last_error", "vfe_debug_tc_partials",
     "vfe_get_trace_rows", "vfe_internal_force_noalloc",
     "vfe_create_batch", "vfe_batch_step", "vfe_batch_synchronize", "vfe_destroy_batch",
-    "vfe_misfit_gradient",
+    "vfe_misfit_gradient", "vfe_step_forced",
 )
 
 
@@ -84,6 +84,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_batch_synchronize.argtypes = [P]
     L.vfe_destroy_batch.argtypes = [P]
     L.vfe_step.argtypes = [P, I]
+    L.vfe_step_forced.argtypes = [P, I, P]
     L.vfe_synchronize.argtypes = [P]
     L.vfe_get_traces.argtypes = [P, P, ctypes.POINTER(I64)]
     L.vfe_get_trace_rows.argtypes = [P, I64, I64, P]
@@ -178,6 +179,17 @@ def vfe_internal_force_noalloc(mesh, u):
 
 def vfe_step(mesh, n):
     _check(load().vfe_step(mesh, int(n)))
+
+
+def vfe_step_forced(mesh, force):
+    """Advance len(force) steps with the source-node force rows ``force``
+    ([n][3] FP64; a page-locked array is passed through without a copy)."""
+    if isinstance(force, np.ndarray) and force.dtype == np.float64 and force.flags.c_contiguous:
+        f = force
+    else:
+        f = np.ascontiguousarray(force, dtype=np.float64)
+    f = f.reshape(-1, 3)
+    _check(load().vfe_step_forced(mesh, int(f.shape[0]), f.ctypes.data_as(ctypes.c_void_p)))
 
 
 def vfe_synchronize(mesh):
@@ -331,6 +343,9 @@ class Mesh:
 
     def step(self, n):
         vfe_step(self.handle, n)
+
+    def step_forced(self, force):
+        vfe_step_forced(self.handle, force)
 
     def synchronize(self):
         vfe_synchronize(self.handle)
