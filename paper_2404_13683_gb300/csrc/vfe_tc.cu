@@ -392,6 +392,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     return;
   }
 
+  // a time step is launched as a programmatic dependent of its prologue: the
+  // setup above overlaps the prologue, the step parameters are read after it
+  if constexpr (MODE == TC_MODE_STEP) asm volatile("griddepcontrol.wait;" ::: "memory");
+
   uint32_t uphase = 0;   // parity bit per U slot
   uint32_t mma_phase = 0;
   bool aborted = false;
@@ -490,14 +494,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int Rseg = P.eCref + P.rs - shq - 63;
     const int64_t dbias = (1LL << 10) | (1LL << 21) | (1LL << 32) | (1LL << 43) | (1LL << 54);
     unsigned long long or_seg = 0;
-    auto digitise_task = [&](int p, int t) {
-      const int dk = t & 7;         // node pair in the row
-      const int dc = (t >> 3) % 3;  // component
-      const int dnj = t / 24;       // node row
-      const int64_t *src = uslot + (p & 7) * (kUSlotStride / 8) +
-                           (dc * TC_NODES + dnj) * TC_BOXX + 2 * dk + xo;
-      unsigned char *dst = digits + ((p % kDigitSlots + kDigitSlots) % kDigitSlots) * kDigitSlotBytes +
-                           (dnj * 2 + (dk >> 2)) * kBlockBytes + dc * 16 + (dk & 3) * 4;
+    // task t's offsets in a U slot (int64 words) and in a digit slot (bytes)
+    auto task_src = [&](int t) {
+      return ((t >> 3) % 3 * TC_NODES + t / 24) * TC_BOXX + 2 * (t & 7) + xo;
+    };
+    auto task_dst = [&](int t) {
+      return (t / 24 * 2 + ((t & 7) >> 2)) * kBlockBytes + (t >> 3) % 3 * 16 + (t & 3) * 4;
+    };
+    auto digitise_at = [&](const int64_t *src, unsigned char *dst) {
       uint64_t v[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) v[i] = (uint64_t)((src[i] >> shq) + dbias);
@@ -514,6 +518,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         *reinterpret_cast<__half2 *>(dst + s * kStageBytes + 48) = hi;
       }
     };
+    auto uslot_of = [&](int p) { return uslot + (p & 7) * (kUSlotStride / 8); };
+    auto dslot_of = [&](int p) {
+      return digits + ((p % kDigitSlots + kDigitSlots) % kDigitSlots) * kDigitSlotBytes;
+    };
+    auto digitise_task = [&](int p, int t) {
+      digitise_at(uslot_of(p) + task_src(t), dslot_of(p) + task_dst(t));
+    };
+    // the second half's phase-2 tasks: t0 = tid - 256 and, below 408, t1 = tid
+    const int t0 = tid - TC_THREADS / 2;
+    const bool has_t1 = tid < ntask;
+    const int src0 = task_src(t0 < 0 ? 0 : t0), dst0 = task_dst(t0 < 0 ? 0 : t0);
+    const int src1 = task_src(has_t1 ? tid : 0), dst1 = task_dst(has_t1 ? tid : 0);
     // one thread issues the MMAs of element layer L (node planes L, L+1),
     // tile 0 first, with one commit per tile
     // A (MN-major): 8-element chunks at 128 B, K groups (dy) at 256 B; B (K-major):
@@ -608,7 +624,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // columns per stage, recombined in Horner order while the next stage's
         // words load (two buffers of 12 words)
         const int c0 = 24 * half + 12 * gg;  // 0, 12, 24, 36
-        const bool first8 = (c0 & 7) == 0;
+        const bool first8 = gg == 0;  // c0 = 24 half + 12 gg is 0 mod 8 iff gg = 0
         const int dy = g & 1, dz = g >> 1;
         uint64_t acc[12];
         uint32_t wa[12], wb[12];
@@ -688,8 +704,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       okp = true;
       if (L + 3 <= Llast + 1) okp = wait_plane(L + 3, half == 1);
       if (L + 4 <= Llast + 1) issue_plane(L + 4, TC_THREADS / 2);
-      if (half == 1 && L + 3 <= Llast + 1)
-        for (int t = tid - TC_THREADS / 2; t < ntask; t += TC_THREADS / 2) digitise_task(L + 3, t);
+      if (half == 1 && L + 3 <= Llast + 1) {
+        const int64_t *us = uslot_of(L + 3);
+        unsigned char *ds = dslot_of(L + 3);
+        digitise_at(us + src0, ds + dst0);
+        if (has_t1) digitise_at(us + src1, ds + dst1);
+      }
       if constexpr (MODE == TC_MODE_PARTIALS) continue;
 
       // (e) y reduction from the shared buffer.  Half 1 holds the forces of
@@ -891,9 +911,15 @@ __device__ void prologue_body(const TcPrologueArgs &A) {
   if (A.trace_on) persist[2] += 1;
 }
 
-__global__ void tc_prologue_kernel(const TcPrologueArgs A) { prologue_body(A); }
+// Each prologue lets its step kernel launch at once (that kernel waits for the
+// prologue's results before reading them).
+__global__ void tc_prologue_kernel(const TcPrologueArgs A) {
+  asm volatile("griddepcontrol.launch_dependents;");
+  prologue_body(A);
+}
 
 __global__ void tc_batch_prologue_kernel(const TcPrologueArgs *args) {
+  asm volatile("griddepcontrol.launch_dependents;");
   prologue_body(args[blockIdx.x]);
 }
 
@@ -954,18 +980,34 @@ cudaError_t tc_prepare() {
   return set_attr_all<TC_MODE_PARTIALS, false>();
 }
 
+template <int MODE, int S, bool BATCHED>
+static cudaError_t launch_one(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap,
+                              const TcBatch &b, int n_ctas) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(n_ctas);
+  cfg.blockDim = dim3(TC_THREADS);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = s;
+  // time steps follow their prologue as programmatic dependents
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = MODE == TC_MODE_STEP ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, tc_step_kernel<MODE, S, BATCHED>, *tmap, d, b);
+}
+
 template <int MODE, bool BATCHED>
 static cudaError_t launch_mode(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap,
                                const TcBatch &b, int stages, int n_ctas) {
-  const dim3 grid(n_ctas), block(TC_THREADS);
   switch (stages) {
-    case 1: tc_step_kernel<MODE, 1, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
-    case 2: tc_step_kernel<MODE, 2, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
-    case 3: tc_step_kernel<MODE, 3, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
-    case 4: tc_step_kernel<MODE, 4, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
-    default: tc_step_kernel<MODE, 5, BATCHED><<<grid, block, kSmemBytes, s>>>(*tmap, d, b); break;
+    case 1: return launch_one<MODE, 1, BATCHED>(s, d, tmap, b, n_ctas);
+    case 2: return launch_one<MODE, 2, BATCHED>(s, d, tmap, b, n_ctas);
+    case 3: return launch_one<MODE, 3, BATCHED>(s, d, tmap, b, n_ctas);
+    case 4: return launch_one<MODE, 4, BATCHED>(s, d, tmap, b, n_ctas);
+    default: return launch_one<MODE, 5, BATCHED>(s, d, tmap, b, n_ctas);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode) {
