@@ -58,6 +58,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_ricker.restype = d
         L.oracle_run.argtypes = [i, i, i, i, d, p, p, i, i, d, i, i64, p, d, d, d,
                                  i, p, p, p, p, p, p]
+        L.oracle_run_damped.argtypes = [i, i, i, i, d, p, p, i, i, d, i, i64, p, d, d, d, d, d,
+                                        i, p, p, p, p, p, p]
         L.oracle_misfit_gradient.argtypes = [i, i, i, i, d, p, p, i, i, d, i, i64, p, d, d, d,
                                              i, p, p, p, p]
         _lib = L
@@ -159,8 +161,9 @@ def ricker(t, f0, t0):
 
 
 def run(kind, mesh, dt_, nsteps, source=None, receivers=(), fix_bottom=True,
-        u0=None, um1=None, return_state=False):
-    """Central-difference run; returns traces [nsteps, n_rec, 3] (and state)."""
+        u0=None, um1=None, return_state=False, alpha=0.0, beta=0.0):
+    """Central-difference run; returns traces [nsteps, n_rec, 3] (and state).
+    alpha, beta != 0 run oracle_run_damped (Rayleigh damping C = alpha M + beta K)."""
     mat, tab = _mesh_args(mesh)
     nx, ny, nz = mesh["shape"]
     nn = (nx + 1) * (ny + 1) * (nz + 1)
@@ -177,10 +180,18 @@ def run(kind, mesh, dt_, nsteps, source=None, receivers=(), fix_bottom=True,
     um1 = None if um1 is None else _f64(um1).reshape(-1)
     uo = np.zeros(3 * nn) if return_state else None
     umo = np.zeros(3 * nn) if return_state else None
-    _check(lib().oracle_run(kind, nx, ny, nz, mesh["h"], _ptr(mat), _ptr(tab), len(tab),
-                            int(fix_bottom), dt_, nsteps, src_node, _ptr(sdir), f0, t0, amp,
-                            len(rec), _ptr(rec) if len(rec) else None, _ptr(u0), _ptr(um1),
-                            _ptr(tr) if len(rec) else None, _ptr(uo), _ptr(umo)), "run")
+    if alpha or beta:
+        _check(lib().oracle_run_damped(kind, nx, ny, nz, mesh["h"], _ptr(mat), _ptr(tab),
+                                       len(tab), int(fix_bottom), dt_, nsteps, src_node,
+                                       _ptr(sdir), f0, t0, amp, float(alpha), float(beta),
+                                       len(rec), _ptr(rec) if len(rec) else None, _ptr(u0),
+                                       _ptr(um1), _ptr(tr) if len(rec) else None, _ptr(uo),
+                                       _ptr(umo)), "run_damped")
+    else:
+        _check(lib().oracle_run(kind, nx, ny, nz, mesh["h"], _ptr(mat), _ptr(tab), len(tab),
+                                int(fix_bottom), dt_, nsteps, src_node, _ptr(sdir), f0, t0, amp,
+                                len(rec), _ptr(rec) if len(rec) else None, _ptr(u0), _ptr(um1),
+                                _ptr(tr) if len(rec) else None, _ptr(uo), _ptr(umo)), "run")
     if return_state:
         return tr, uo, umo
     return tr

@@ -651,6 +651,68 @@ done:
   return rc;
 }
 
+/* ---------- central-difference run with Rayleigh damping ------------------ */
+
+int oracle_run_damped(int kind, int nx, int ny, int nz, double ds,
+                      const int32_t *mat, const double *table, int n_mat,
+                      int fix_bottom, double dt, int nsteps,
+                      int64_t src_node, const double *src_dir, double f0,
+                      double t0, double amp, double alpha, double beta,
+                      int n_rec, const int64_t *rec_nodes,
+                      const double *u0, const double *um1,
+                      double *traces, double *u_out, double *um1_out) {
+  if (check_mesh(nx, ny, nz, mat, n_mat) || !(dt > 0.0) || nsteps < 0) return -1;
+  if (!(alpha >= 0.0) || !(beta >= 0.0)) return -1;
+  if (n_rec < 0 || (n_rec > 0 && (!rec_nodes || !traces))) return -1;
+  int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  if (src_node >= nn) return -1;
+  for (int r = 0; r < n_rec; ++r)
+    if (rec_nodes[r] < 0 || rec_nodes[r] >= nn) return -1;
+  double *mass = (double *)malloc(sizeof(double) * nn);
+  double *u = (double *)malloc(sizeof(double) * 3 * nn);
+  double *up = (double *)malloc(sizeof(double) * 3 * nn);
+  double *un = (double *)malloc(sizeof(double) * 3 * nn);
+  double *w = (double *)malloc(sizeof(double) * 3 * nn);
+  double *f = (double *)malloc(sizeof(double) * 3 * nn);
+  char *fixed = (char *)malloc((size_t)nn);
+  const double a = 0.5 * alpha * dt, b = beta / dt;
+  int rc = -1;
+  if (!mass || !u || !up || !un || !w || !f || !fixed) goto done;
+  if (oracle_node_mass(kind, nx, ny, nz, ds, mat, table, n_mat, mass)) goto done;
+  for (int64_t n = 0; n < nn; ++n) {
+    int nk = (int)(n / ((int64_t)(nx + 1) * (ny + 1)));
+    fixed[n] = (char)((fix_bottom && nk == 0) || mass[n] == 0.0);
+  }
+  for (int64_t d = 0; d < 3 * nn; ++d) {
+    u[d] = u0 ? u0[d] : 0.0;
+    up[d] = um1 ? um1[d] : 0.0;
+    if (fixed[d / 3]) u[d] = up[d] = 0.0;
+  }
+  for (int it = 0; it < nsteps; ++it) {
+    /* K acts on u plus beta times the backward velocity */
+    for (int64_t d = 0; d < 3 * nn; ++d) w[d] = u[d] + b * (u[d] - up[d]);
+    if (oracle_ku(kind, nx, ny, nz, ds, mat, table, n_mat, 0, w, f)) goto done;
+    double fsrc = src_node >= 0 ? amp * oracle_ricker(it * dt, f0, t0) : 0.0;
+    for (int64_t n = 0; n < nn; ++n)
+      for (int c = 0; c < 3; ++c) {
+        int64_t d = 3 * n + c;
+        if (fixed[n]) { un[d] = 0.0; continue; }
+        double F = (n == src_node) ? fsrc * src_dir[c] : 0.0;
+        un[d] = (2.0 * u[d] - (1.0 - a) * up[d] + dt * dt / mass[n] * (F - f[d])) / (1.0 + a);
+      }
+    for (int r = 0; r < n_rec; ++r)
+      for (int c = 0; c < 3; ++c)
+        traces[((int64_t)it * n_rec + r) * 3 + c] = un[3 * rec_nodes[r] + c];
+    double *t = up; up = u; u = un; un = t;
+  }
+  if (u_out) memcpy(u_out, u, sizeof(double) * 3 * nn);
+  if (um1_out) memcpy(um1_out, up, sizeof(double) * 3 * nn);
+  rc = 0;
+done:
+  free(mass); free(u); free(up); free(un); free(w); free(f); free(fixed);
+  return rc;
+}
+
 /* ---------- adjoint-state gradient (plain loops, all states stored) ------ */
 
 int oracle_misfit_gradient(int kind, int nx, int ny, int nz, double ds,

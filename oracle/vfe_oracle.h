@@ -115,6 +115,23 @@ int oracle_run(int kind, int nx, int ny, int nz, double ds,
                const double *u0, const double *um1,
                double *traces, double *u_out, double *um1_out);
 
+/* oracle_run with Rayleigh damping C = alpha M + beta K (Section 3 uses
+ * Rayleigh damping without giving its time discretisation; the reading used
+ * here): the mass term with the central velocity (u^{n+1} - u^{n-1}) / (2 dt),
+ * the stiffness term with the backward velocity (u^n - u^{n-1}) / dt, so the
+ * step stays explicit:
+ *   (1 + a) u^{n+1} = 2 u^n - (1 - a) u^{n-1} - dt^2 M^-1 (K w^n - F^n),
+ *   a = alpha dt / 2,  w^n = u^n + (beta / dt) (u^n - u^{n-1}).
+ * alpha = beta = 0 gives oracle_run exactly. */
+int oracle_run_damped(int kind, int nx, int ny, int nz, double ds,
+                      const int32_t *mat, const double *table, int n_mat,
+                      int fix_bottom, double dt, int nsteps,
+                      int64_t src_node, const double *src_dir, double f0,
+                      double t0, double amp, double alpha, double beta,
+                      int n_rec, const int64_t *rec_nodes,
+                      const double *u0, const double *um1,
+                      double *traces, double *u_out, double *um1_out);
+
 /* Adjoint-state gradient of the receiver misfit
  *   J = 1/2 sum_{n<N} sum_r |u^{n+1}(r) - data[n][r]|^2
  * for the run of oracle_run (from rest), with respect to each element's shear
