@@ -113,6 +113,26 @@ int vfe_step(vfe_mesh *mesh, int n);
  * (growing the device copy of the rows), VFE_ECUDA. */
 int vfe_step_forced(vfe_mesh *mesh, int n, const double *force);
 
+/* Rayleigh damping C = alpha M + beta K (Section 3 computes attenuation with
+ * Rayleigh damping; it gives no time discretisation, and this library uses
+ * the one that keeps the step explicit with the diagonal mass):
+ *   (1 + a) u^{n+1} = 2 u^n - (1 - a) u^{n-1} - dt^2 M^-1 (K w^n - F^n),
+ *   a = alpha dt / 2,  w^n = u^n + (beta / dt) (u^n - u^{n-1}),
+ * i.e. the mass term with the central velocity and the stiffness term with
+ * the backward velocity.  alpha = beta = 0 (the default) is the undamped
+ * step.  Needs alpha, beta >= 0, alpha dt / 2 < 1 and, for stability,
+ * (dt / dt_crit)^2 (1 + 2 beta / dt) <= 1 (VFE_EINVAL otherwise).  Takes
+ * effect from the next step (the current state is kept).  Not combined with
+ * vfe_misfit_gradient (VFE_ESTATE).  Synchronous. */
+int vfe_set_damping(vfe_mesh *mesh, double alpha, double beta);
+
+/* The Rayleigh coefficients that give damping ratio h at the frequencies f1
+ * and f2 (Hz, 0 < f1 <= f2): alpha = 2 h w1 w2 / (w1 + w2),
+ * beta = 2 h / (w1 + w2), w = 2 pi f; between f1 and f2 the ratio
+ * alpha / (2 w) + beta w / 2 stays below h.  Host only (no GPU needed). */
+int vfe_rayleigh_coefficients(double h, double f1_hz, double f2_hz, double *alpha,
+                              double *beta);
+
 /* Block until queued work is done; reports device-side timeouts. */
 int vfe_synchronize(vfe_mesh *mesh);
 

@@ -130,6 +130,12 @@ struct vfe_mesh {
   std::vector<double> mass;
   std::vector<char> fixed;
   double dt = 0.0;
+  double dt_crit = 0.0;  // 2 / sqrt(max eigenvalue of M_e^-1 K_e) over the materials
+  double alpha = 0.0, beta = 0.0;  // Rayleigh damping C = alpha M + beta K
+  bool damped = false;
+  double *d_w[2] = {nullptr, nullptr};  // FP64 path: w^n, w^{n+1} (damped only)
+  int64_t *d_W[2] = {nullptr, nullptr};  // TC path: the same in the state's fixed point
+  CUtensorMap tmap_w[2];                 // TMA maps over d_W (damped TC path)
   int64_t steps = 0;  // host mirror of the device step counter
 
   int32_t *d_mat = nullptr;
@@ -221,6 +227,15 @@ static TcDevice tc_device(const vfe_mesh *m, int cur) {
   d.tiles_x = m->tiles_x; d.tiles_y = m->tiles_y;
   d.params = m->d_tcparams;
   d.inj = m->d_inj;
+  d.damped = m->damped ? 1 : 0;
+  if (m->damped) {
+    const double a = 0.5 * m->alpha * m->dt, g = 1.0 / (1.0 + a);
+    d.U_cur = m->d_U[cur];
+    d.W_next = m->d_W[1 - cur];
+    d.dG = llrint(std::ldexp(g, 62));
+    d.dH = llrint(std::ldexp((1.0 - a) * g, 62));
+    d.dB = llrint(std::ldexp(m->beta / m->dt, 62));
+  }
   return d;
 }
 
@@ -233,6 +248,11 @@ static F64Device f64_device(const vfe_mesh *m, int cur) {
   d.dt2_m = m->d_dt2m; d.recv_nodes = m->d_recnodes; d.traces = m->d_traces;
   d.src_node = m->has_src ? m->src_node : -1;
   d.inj = m->d_inj;
+  d.damped = m->damped ? 1 : 0;
+  d.w = m->d_w[cur];
+  d.w_next = m->d_w[1 - cur];
+  d.da = 0.5 * m->alpha * m->dt;
+  d.db = m->beta / m->dt;
   return d;
 }
 
@@ -247,13 +267,16 @@ static int enqueue_step(vfe_mesh *m, int cur) {
   src.force = m->d_force;
   src.force_rows = m->force_cap;
   if (m->opt.path == VFE_PATH_TC) {
-    src.amp_scale = m->amp * m->src_scale;
-    src.force_scale = m->src_scale;
+    // with damping the step's increments carry the factor 1 / (1 + alpha dt / 2)
+    const double g = m->damped ? 1.0 / (1.0 + 0.5 * m->alpha * m->dt) : 1.0;
+    src.amp_scale = m->amp * m->src_scale * g;
+    src.force_scale = m->src_scale * g;
     CUDA_TRY(tc_launch_prologue_ex(m->stream, m->d_tcparams, m->d_tcpersist, src, m->d_or,
                                    m->tiles_x * m->tiles_y, m->has_src ? 1 : 0, trace_on,
                                    m->d_status, m->d_inj, 3 * m->n_rec));
     TcDevice d = tc_device(m, cur);
-    CUDA_TRY(tc_launch_step(m->stream, d, &m->tmap[cur], TC_MODE_STEP));
+    CUDA_TRY(tc_launch_step(m->stream, d, m->damped ? &m->tmap_w[cur] : &m->tmap[cur],
+                            TC_MODE_STEP));
   } else {
     src.amp_scale = m->amp;
     src.force_scale = 1.0;
@@ -321,7 +344,8 @@ int vfe_destroy(vfe_mesh *m) {
                   m->d_dt2m, m->d_K, m->d_recnodes, m->d_f64params, m->d_f64persist,
                   m->d_U[0], m->d_U[1], m->d_C, m->d_Bop, m->d_mats, m->d_recv,
                   m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist, m->d_segs,
-                  m->d_seg_off, m->d_inj, m->d_force};
+                  m->d_seg_off, m->d_inj, m->d_force, m->d_w[0], m->d_w[1],
+                  m->d_W[0], m->d_W[1]};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -422,6 +446,7 @@ int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_id
     return fail(VFE_EINVAL, "the mesh has no solid element");
   }
   m->dt = opt.dt > 0.0 ? opt.dt : opt.cfl_fraction * dtc;
+  m->dt_crit = dtc;
 
   cudaError_t e = cudaSetDevice(m->device);
   if (e != cudaSuccess) {
@@ -487,6 +512,30 @@ static int build_f64(vfe_mesh *m) {
   CUDA_TRY(cudaMemset(m->d_u[1], 0, sizeof(double) * 3 * m->nn));
   const int64_t f64persist[6] = {0, 0, -1, 0, -1, 0};
   CUDA_TRY(cudaMemcpy(m->d_f64persist, f64persist, sizeof(f64persist), cudaMemcpyHostToDevice));
+  return VFE_OK;
+}
+
+// per-node update multiplier round(g dt^2/m 2^eC) in the padded SoA layout,
+// g = 1 / (1 + alpha dt / 2) with damping (1 without); 0 at fixed nodes
+static std::vector<int64_t> tc_update_multipliers(const vfe_mesh *m) {
+  const double g = m->damped ? 1.0 / (1.0 + 0.5 * m->alpha * m->dt) : 1.0;
+  std::vector<int64_t> C(m->plane * (m->nz + 1), 0);
+  for (int64_t n = 0; n < m->nn; ++n)
+    if (!m->fixed[n]) C[tc_index(m, n)] = llrint(std::ldexp(g * m->dt * m->dt / m->mass[n], m->eC));
+  return C;
+}
+
+// TMA map over a padded SoA int64 nodal array: (x, y, z, component), box 18x17x1x3
+static int encode_state_tmap(const vfe_mesh *m, EncodeTiledFn enc, void *base, CUtensorMap *map) {
+  cuuint64_t dims[4] = {(cuuint64_t)m->nxp, (cuuint64_t)m->nyp, (cuuint64_t)(m->nz + 1), 3};
+  cuuint64_t strides[3] = {(cuuint64_t)m->nxp * 8, (cuuint64_t)m->plane * 8,
+                           (cuuint64_t)m->comp * 8};
+  cuuint32_t box[4] = {TC_BOXX, TC_NODES, 1, 3};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return VFE_OK;
 }
 
@@ -558,9 +607,7 @@ static int build_tc(vfe_mesh *m) {
   m->nyp = std::max(ny + 1, TC_NODES);
   m->plane = (int64_t)m->nxp * m->nyp;
   m->comp = m->plane * (nz + 1);
-  std::vector<int64_t> C(m->plane * (nz + 1), 0);
-  for (int64_t n = 0; n < m->nn; ++n)
-    if (!m->fixed[n]) C[tc_index(m, n)] = llrint(std::ldexp(m->dt * m->dt / m->mass[n], m->eC));
+  std::vector<int64_t> C = tc_update_multipliers(m);
   // work decomposition: the column-planes (15x15 node column, one node
   // plane) in column order are split into one equal contiguous range per SM;
   // each range becomes one or more segments (column, z0, z1)
@@ -618,15 +665,8 @@ static int build_tc(vfe_mesh *m) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled is not available");
   for (int b = 0; b < 2; ++b) {
-    cuuint64_t dims[4] = {(cuuint64_t)m->nxp, (cuuint64_t)m->nyp, (cuuint64_t)(nz + 1), 3};
-    cuuint64_t strides[3] = {(cuuint64_t)m->nxp * 8, (cuuint64_t)m->plane * 8,
-                             (cuuint64_t)m->comp * 8};
-    cuuint32_t box[4] = {TC_BOXX, TC_NODES, 1, 3};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    CUresult r = enc(&m->tmap[b], CU_TENSOR_MAP_DATA_TYPE_INT64, 4, m->d_U[b], dims, strides, box,
-                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    const int rc = encode_state_tmap(m, enc, m->d_U[b], &m->tmap[b]);
+    if (rc != VFE_OK) return rc;
   }
   return VFE_OK;
 }
@@ -928,10 +968,21 @@ int vfe_set_state(vfe_mesh *m, const double *u, const double *u_prev) {
                         cudaMemcpyHostToDevice));
     // the next step reads slot (step + 2) % 3: the global bound of |u^n|,
     // |u^{n-1}| and one bound per 15x15 node column (its digit quantum)
+    // with damping the digitised vector is w^n = u^n + (beta / dt)(u^n - u^{n-1})
+    std::vector<int64_t> W0;
+    unsigned long long ow = 0;
+    if (m->damped) {
+      const double bb = m->beta / m->dt;
+      std::vector<double> w(3 * m->nn);
+      for (size_t i = 0; i < w.size(); ++i) w[i] = u[i] + bb * (u[i] - u_prev[i]);
+      to_fixed(m, w.data(), F, W0, true, &ow);
+      CUDA_TRY(cudaMemcpy(m->d_W[m->cur], W0.data(), sizeof(int64_t) * W0.size(),
+                          cudaMemcpyHostToDevice));
+    }
     const int ncols = m->tiles_x * m->tiles_y;
     std::vector<unsigned long long> slots(3 * (size_t)(1 + ncols), 0);
     unsigned long long *sl = slots.data() + (size_t)((m->steps + 2) % 3) * (1 + ncols);
-    sl[0] = o0 | o1;
+    sl[0] = o0 | o1 | ow;
     for (int64_t n = 0; n < m->nn; ++n) {
       const int64_t i = n % (m->nx + 1), j = (n / (m->nx + 1)) % (m->ny + 1);
       const int64_t t = tc_index(m, n);
@@ -939,6 +990,10 @@ int vfe_set_state(vfe_mesh *m, const double *u, const double *u_prev) {
       for (int c = 0; c < 3; ++c) {
         const int64_t a = U0[c * m->comp + t], b = U1[c * m->comp + t];
         o |= (unsigned long long)(a < 0 ? -a : a) | (unsigned long long)(b < 0 ? -b : b);
+        if (m->damped) {
+          const int64_t w = W0[c * m->comp + t];
+          o |= (unsigned long long)(w < 0 ? -w : w);
+        }
       }
       sl[1 + (j / TC_OWN) * m->tiles_x + (i / TC_OWN)] |= o;
     }
@@ -956,8 +1011,71 @@ int vfe_set_state(vfe_mesh *m, const double *u, const double *u_prev) {
                         cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(m->d_u[1 - m->cur], b.data(), sizeof(double) * b.size(),
                         cudaMemcpyHostToDevice));
+    if (m->damped) {  // w^n = u^n + (beta / dt) (u^n - u^{n-1})
+      const double bb = m->beta / m->dt;
+      std::vector<double> w(a.size());
+      for (size_t i = 0; i < w.size(); ++i) w[i] = a[i] + bb * (a[i] - b[i]);
+      CUDA_TRY(cudaMemcpy(m->d_w[m->cur], w.data(), sizeof(double) * w.size(),
+                          cudaMemcpyHostToDevice));
+    }
   }
   return VFE_OK;
+}
+
+int vfe_rayleigh_coefficients(double h, double f1_hz, double f2_hz, double *alpha,
+                              double *beta) {
+  if (!alpha || !beta) return fail(VFE_EINVAL, "NULL output");
+  if (!(h >= 0.0) || !std::isfinite(h) || !(f1_hz > 0.0) || !(f2_hz >= f1_hz) ||
+      !std::isfinite(f2_hz))
+    return fail(VFE_EINVAL, "need h >= 0 and 0 < f1 <= f2");
+  const double w1 = 2.0 * M_PI * f1_hz, w2 = 2.0 * M_PI * f2_hz;
+  *alpha = 2.0 * h * w1 * w2 / (w1 + w2);
+  *beta = 2.0 * h / (w1 + w2);
+  return VFE_OK;
+}
+
+int vfe_set_damping(vfe_mesh *m, double alpha, double beta) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  if (!(alpha >= 0.0) || !(beta >= 0.0) || !std::isfinite(alpha) || !std::isfinite(beta))
+    return fail(VFE_EINVAL, "need finite alpha >= 0 and beta >= 0");
+  const double a = 0.5 * alpha * m->dt, b = beta / m->dt, r = m->dt / m->dt_crit;
+  if (a >= 1.0) return fail(VFE_EINVAL, "alpha dt / 2 = %g must be below 1", a);
+  if (r * r * (1.0 + 2.0 * b) > 1.0)
+    return fail(VFE_EINVAL,
+                "unstable: (dt / dt_crit)^2 (1 + 2 beta / dt) = %g exceeds 1 (dt %g, dt_crit %g)",
+                r * r * (1.0 + 2.0 * b), m->dt, m->dt_crit);
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  // rebuild w from the current state with the new coefficients
+  std::vector<double> u(3 * m->nn), up(3 * m->nn);
+  int rc = vfe_get_state(m, u.data(), up.data());
+  if (rc != VFE_OK) return rc;
+  const bool damped = alpha > 0.0 || beta > 0.0;
+  if (damped && m->opt.path == VFE_PATH_FP64 && !m->d_w[0]) {
+    for (int i = 0; i < 2; ++i)
+      if (cudaMalloc(&m->d_w[i], sizeof(double) * 3 * m->nn) != cudaSuccess)
+        return fail(VFE_ENOMEM, "damping state");
+  }
+  if (damped && m->opt.path == VFE_PATH_TC && !m->d_W[0]) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled is not available");
+    for (int i = 0; i < 2; ++i) {
+      if (cudaMalloc(&m->d_W[i], sizeof(int64_t) * 3 * m->comp) != cudaSuccess)
+        return fail(VFE_ENOMEM, "damping state");
+      CUDA_TRY(cudaMemset(m->d_W[i], 0, sizeof(int64_t) * 3 * m->comp));
+      rc = encode_state_tmap(m, enc, m->d_W[i], &m->tmap_w[i]);
+      if (rc != VFE_OK) return rc;
+    }
+  }
+  m->alpha = alpha;
+  m->beta = beta;
+  m->damped = damped;
+  if (m->opt.path == VFE_PATH_TC) {  // the update multipliers carry 1 / (1 + alpha dt / 2)
+    const std::vector<int64_t> C = tc_update_multipliers(m);
+    CUDA_TRY(cudaMemcpy(m->d_C, C.data(), sizeof(int64_t) * C.size(), cudaMemcpyHostToDevice));
+  }
+  invalidate_graphs(m);
+  return vfe_set_state(m, u.data(), up.data());
 }
 
 int vfe_get_state(vfe_mesh *m, double *u, double *u_prev) {
@@ -1343,6 +1461,8 @@ int vfe_create_batch(int n, vfe_mesh *const *meshes, vfe_batch **out) {
       return fail(VFE_EINVAL, "mesh %d is not on the tensor-core path", i);
     if (meshes[i]->device != meshes[0]->device)
       return fail(VFE_EINVAL, "mesh %d is on another device", i);
+    if (meshes[i]->damped)
+      return fail(VFE_EINVAL, "mesh %d is damped: batches step undamped meshes only", i);
     if (meshes[i]->opt.stages != meshes[0]->opt.stages)
       return fail(VFE_EINVAL, "mesh %d uses %d digit stages, mesh 0 uses %d", i,
                   meshes[i]->opt.stages, meshes[0]->opt.stages);
@@ -1587,6 +1707,7 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
   if (!m || !data || !grad_G) return fail(VFE_EINVAL, "NULL argument");
   if (nsteps < 1 || checkpoint_every < 1) return fail(VFE_EINVAL, "need nsteps, checkpoint >= 1");
   if (m->n_rec < 1) return fail(VFE_ESTATE, "the misfit needs receivers");
+  if (m->damped) return fail(VFE_ESTATE, "the misfit gradient supports undamped meshes only");
   cudaSetDevice(m->device);
   CUDA_TRY(cudaStreamSynchronize(m->stream));
   const int N = nsteps, C = checkpoint_every, nr = m->n_rec;

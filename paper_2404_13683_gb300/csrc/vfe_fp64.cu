@@ -6,7 +6,10 @@
 // One thread per node gathers the rows of its (up to) eight elements, so the
 // node sums need no atomics and the update is fused into the same pass.
 // The path is FP64-bound (576 FMA per node), which is the point: it is the
-// baseline the integer tensor-core path is measured against.
+// baseline the integer tensor-core path is measured against.  With Rayleigh
+// damping the gather reads w^n = u^n + (beta/dt)(u^n - u^{n-1}) (kept as a
+// state array, since u^{n-1} is overwritten in place) and the update divides
+// by 1 + alpha dt / 2.
 #include "vfe_internal.h"
 
 struct F64StepParams {
@@ -56,6 +59,7 @@ __global__ void __launch_bounds__(256) f64_step_kernel(const F64Device d, const 
        n += (int64_t)gridDim.x * blockDim.x) {
     const int ni = (int)(n % sx), nj = (int)((n / sx) % (ny + 1)), nk = (int)(n / sxy);
     double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    const double *x = d.damped ? d.w : d.u;  // the vector K acts on
     for (int a = 0; a < 8; ++a) {
       const int ex = ni - (a & 1), ey = nj - ((a >> 1) & 1), ez = nk - (a >> 2);
       if (ex < 0 || ey < 0 || ez < 0 || ex >= nx || ey >= ny || ez >= nz) continue;
@@ -64,7 +68,7 @@ __global__ void __launch_bounds__(256) f64_step_kernel(const F64Device d, const 
       const double *K = sK + m * 576 + (3 * a) * 24;
       for (int b = 0; b < 8; ++b) {
         const int64_t nb = (ex + (b & 1)) + sx * (ey + ((b >> 1) & 1)) + sxy * (ez + (b >> 2));
-        const double u0 = d.u[3 * nb], u1 = d.u[3 * nb + 1], u2 = d.u[3 * nb + 2];
+        const double u0 = x[3 * nb], u1 = x[3 * nb + 1], u2 = x[3 * nb + 2];
         const double *k0 = K + 3 * b, *k1 = K + 24 + 3 * b, *k2 = K + 48 + 3 * b;
         f0 = fma(k0[0], u0, fma(k0[1], u1, fma(k0[2], u2, f0)));
         f1 = fma(k1[0], u0, fma(k1[1], u1, fma(k1[2], u2, f1)));
@@ -84,7 +88,11 @@ __global__ void __launch_bounds__(256) f64_step_kernel(const F64Device d, const 
     double un[3];
     for (int k = 0; k < 3; ++k) {
       const double F = src ? p.src[k] : 0.0;
-      un[k] = 2.0 * d.u[3 * n + k] - d.u_prev[3 * n + k] + c * (F - fv[k]);
+      if (d.damped)
+        un[k] = (2.0 * d.u[3 * n + k] - (1.0 - d.da) * d.u_prev[3 * n + k] + c * (F - fv[k])) /
+                (1.0 + d.da);
+      else
+        un[k] = 2.0 * d.u[3 * n + k] - d.u_prev[3 * n + k] + c * (F - fv[k]);
     }
     if (p.inj_row >= 0)  // injected increments at receiver nodes (adjoint source)
       for (int r = 0; r < d.n_rec; ++r)
@@ -92,6 +100,7 @@ __global__ void __launch_bounds__(256) f64_step_kernel(const F64Device d, const 
           for (int k = 0; k < 3; ++k) un[k] += d.inj[(p.inj_row * d.n_rec + r) * 3 + k];
     for (int k = 0; k < 3; ++k) {
       if (c == 0.0) un[k] = 0.0;
+      if (d.damped) d.w_next[3 * n + k] = un[k] + d.db * (un[k] - d.u[3 * n + k]);
       d.u_next[3 * n + k] = un[k];
     }
     if (p.trace_row >= 0) {

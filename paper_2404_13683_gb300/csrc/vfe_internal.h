@@ -90,6 +90,16 @@ struct TcDevice {         // everything the TC kernels read (by value)
   const double *inj;      // [rows][n_rec][3] displacement increments at the receivers
   int64_t *S_out;         // K u mode: per-node S (int64 x 3, SoA like U)
   int64_t *partials_out;  // partials mode: per element 48 int64 (element order)
+  // Rayleigh damping (damped != 0; the TMA map then covers W = w^n instead of
+  // u^n, see F64Device): u^n of the updated node comes from U_cur, and with
+  // g = 1 / (1 + a) folded into C and the source,
+  //   u^{n+1} = 2 g u^n - (1 - a) g u^{n-1} - C S,  w^{n+1} = u^{n+1} + b (u^{n+1} - u^n),
+  // using the fixed-point constants dG = round(g 2^62),
+  // dH = round((1 - a) g 2^62), dB = round(b 2^62)
+  const int64_t *U_cur;
+  int64_t *W_next;
+  int64_t dG, dH, dB;
+  int damped;
 };
 
 // Several meshes advanced by one launch: each segment belongs to one mesh,
@@ -136,6 +146,12 @@ struct F64Device {
   int64_t src_node;
   double *f_out;          // K u mode output
   const double *inj;      // [rows][n_rec][3] displacement increments at the receivers
+  // Rayleigh damping (damped != 0): K acts on w^n = u^n + b (u^n - u^{n-1});
+  // (1 + a) u^{n+1} = 2 u^n - (1 - a) u^{n-1} + dt^2/m (F - K w^n)
+  const double *w;        // w^n [nn][3]
+  double *w_next;         // w^{n+1}
+  double da, db;          // a = alpha dt / 2, b = beta / dt
+  int damped;
 };
 
 // Ricker point source (Section 3 applies an impulse force in z):

@@ -317,7 +317,7 @@ __device__ __forceinline__ int64_t mul_hi63(int64_t P, int C1, int C0) {
 // 15x15 node column (tx, ty) and a range of owned node planes [z0, z1).  The
 // host balances column-planes across CTAs, so every SM gets the same work.
 // ---------------------------------------------------------------------------
-template <int MODE, int STAGES, bool BATCHED>
+template <int MODE, int STAGES, bool BATCHED, bool DAMPED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_step_kernel(const __grid_constant__ CUtensorMap tmap_u, const TcDevice d0,
                    const TcBatch b) {
@@ -594,13 +594,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int L = Lfirst; L <= Llast; ++L) {
       const int m = m_next;
       m_next = mat_at(L + 1);
-      int64_t uprev[3] = {0, 0, 0}, cn = 0;
+      int64_t uprev[3] = {0, 0, 0}, cn = 0, ucur_g[3] = {0, 0, 0};
       const bool upd = (MODE == TC_MODE_STEP) && updater && L >= Z0;
       const int64_t nidx = (int64_t)L * d.plane + (int64_t)gj * d.nxp + gi;
       if (upd) {
         cn = d.C[nidx];
 #pragma unroll
         for (int c = 0; c < 3; ++c) uprev[c] = d.U_prev[c * d.comp + nidx];
+        if constexpr (DAMPED) {  // the U slots hold w^n: u^n of this node from memory
+#pragma unroll
+          for (int c = 0; c < 3; ++c) ucur_g[c] = d.U_cur[c * d.comp + nidx];
+        }
       }
 
       // (b) wait for this warp's tile of MMA(L)
@@ -750,7 +754,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           int64_t unew[3], uold[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            int64_t u0 = ucur[(c * TC_NODES + ej + 1) * TC_BOXX + ei + 1 + xo];
+            int64_t u0 = DAMPED ? ucur_g[c] : ucur[(c * TC_NODES + ej + 1) * TC_BOXX + ei + 1 + xo];
             int64_t um = uprev[c];
             if (rescaled) {
               u0 = shr_round(u0, P.rs);
@@ -769,7 +773,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 du = (int64_t)(prod << min(-Rseg, 63));
               }
             }
-            int64_t un = 2 * u0 - um - du;
+            int64_t un;
+            if constexpr (DAMPED) {  // 2 g u^n - (1 - a) g u^{n-1} - C S, rounded
+              const int64_t t0 = (int64_t)(((__int128)u0 * d.dG + ((__int128)1 << 60)) >> 61);
+              const int64_t t1 = (int64_t)(((__int128)um * d.dH + ((__int128)1 << 61)) >> 62);
+              un = t0 - t1 - du;
+            } else {
+              un = 2 * u0 - um - du;
+            }
             if (is_src) un += P.dU_src[c];
             unew[c] = un;
             uold[c] = u0;
@@ -788,6 +799,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int c = 0; c < 3; ++c) {
             if (cn == 0) unew[c] = 0;  // fixed or massless node
             d.U_next[c * d.comp + nidx] = unew[c];
+            if constexpr (DAMPED) {  // w^{n+1} = u^{n+1} + b (u^{n+1} - u^n), bounded too
+              const int64_t wn =
+                  unew[c] + (int64_t)(((__int128)(unew[c] - uold[c]) * d.dB + ((__int128)1 << 61)) >> 62);
+              d.W_next[c * d.comp + nidx] = wn;
+              or_seg |= (unsigned long long)(wn < 0 ? -wn : wn);
+            }
             // the slot bounds u^{n+1} and u^n (both in the new units)
             or_seg |= (unsigned long long)(unew[c] < 0 ? -unew[c] : unew[c]) |
                       (unsigned long long)(uold[c] < 0 ? -uold[c] : uold[c]);
@@ -958,7 +975,13 @@ cudaError_t tc_launch_batch_prologue(cudaStream_t s, const TcPrologueArgs *args,
 
 template <int MODE, int S, bool BATCHED>
 static cudaError_t set_attr() {
-  return cudaFuncSetAttribute(tc_step_kernel<MODE, S, BATCHED>,
+  return cudaFuncSetAttribute(tc_step_kernel<MODE, S, BATCHED, false>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+template <int S>
+static cudaError_t set_attr_damped() {
+  return cudaFuncSetAttribute(tc_step_kernel<TC_MODE_STEP, S, false, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
@@ -977,10 +1000,14 @@ cudaError_t tc_prepare() {
   if ((e = set_attr_all<TC_MODE_STEP, false>()) != cudaSuccess) return e;
   if ((e = set_attr_all<TC_MODE_STEP, true>()) != cudaSuccess) return e;
   if ((e = set_attr_all<TC_MODE_KU, false>()) != cudaSuccess) return e;
-  return set_attr_all<TC_MODE_PARTIALS, false>();
+  if ((e = set_attr_all<TC_MODE_PARTIALS, false>()) != cudaSuccess) return e;
+  for (cudaError_t (*f)() : {&set_attr_damped<1>, &set_attr_damped<2>, &set_attr_damped<3>,
+                             &set_attr_damped<4>, &set_attr_damped<5>})
+    if ((e = f()) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
-template <int MODE, int S, bool BATCHED>
+template <int MODE, int S, bool BATCHED, bool DAMPED = false>
 static cudaError_t launch_one(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap,
                               const TcBatch &b, int n_ctas) {
   cudaLaunchConfig_t cfg;
@@ -995,18 +1022,18 @@ static cudaError_t launch_one(cudaStream_t s, const TcDevice &d, const CUtensorM
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = MODE == TC_MODE_STEP ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, tc_step_kernel<MODE, S, BATCHED>, *tmap, d, b);
+  return cudaLaunchKernelEx(&cfg, tc_step_kernel<MODE, S, BATCHED, DAMPED>, *tmap, d, b);
 }
 
-template <int MODE, bool BATCHED>
+template <int MODE, bool BATCHED, bool DAMPED = false>
 static cudaError_t launch_mode(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap,
                                const TcBatch &b, int stages, int n_ctas) {
   switch (stages) {
-    case 1: return launch_one<MODE, 1, BATCHED>(s, d, tmap, b, n_ctas);
-    case 2: return launch_one<MODE, 2, BATCHED>(s, d, tmap, b, n_ctas);
-    case 3: return launch_one<MODE, 3, BATCHED>(s, d, tmap, b, n_ctas);
-    case 4: return launch_one<MODE, 4, BATCHED>(s, d, tmap, b, n_ctas);
-    default: return launch_one<MODE, 5, BATCHED>(s, d, tmap, b, n_ctas);
+    case 1: return launch_one<MODE, 1, BATCHED, DAMPED>(s, d, tmap, b, n_ctas);
+    case 2: return launch_one<MODE, 2, BATCHED, DAMPED>(s, d, tmap, b, n_ctas);
+    case 3: return launch_one<MODE, 3, BATCHED, DAMPED>(s, d, tmap, b, n_ctas);
+    case 4: return launch_one<MODE, 4, BATCHED, DAMPED>(s, d, tmap, b, n_ctas);
+    default: return launch_one<MODE, 5, BATCHED, DAMPED>(s, d, tmap, b, n_ctas);
   }
 }
 
@@ -1015,6 +1042,7 @@ cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap 
   memset(&none, 0, sizeof(none));
   switch (mode) {
     case TC_MODE_STEP:
+      if (d.damped) return launch_mode<TC_MODE_STEP, false, true>(s, d, tmap, none, d.stages, d.n_ctas);
       return launch_mode<TC_MODE_STEP, false>(s, d, tmap, none, d.stages, d.n_ctas);
     case TC_MODE_KU: return launch_mode<TC_MODE_KU, false>(s, d, tmap, none, d.stages, d.n_ctas);
     default: return launch_mode<TC_MODE_PARTIALS, false>(s, d, tmap, none, d.stages, d.n_ctas);

@@ -34,7 +34,7 @@ EXPORTS = (
     "vfe_get_state", "vfe_set_state", "vfe_last_error", "vfe_debug_tc_partials",
     "vfe_get_trace_rows", "vfe_internal_force_noalloc",
     "vfe_create_batch", "vfe_batch_step", "vfe_batch_synchronize", "vfe_destroy_batch",
-    "vfe_misfit_gradient", "vfe_step_forced",
+    "vfe_misfit_gradient", "vfe_step_forced", "vfe_set_damping", "vfe_rayleigh_coefficients",
 )
 
 
@@ -85,6 +85,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_destroy_batch.argtypes = [P]
     L.vfe_step.argtypes = [P, I]
     L.vfe_step_forced.argtypes = [P, I, P]
+    L.vfe_set_damping.argtypes = [P, D, D]
+    L.vfe_rayleigh_coefficients.argtypes = [D, D, D, ctypes.POINTER(D), ctypes.POINTER(D)]
     L.vfe_synchronize.argtypes = [P]
     L.vfe_get_traces.argtypes = [P, P, ctypes.POINTER(I64)]
     L.vfe_get_trace_rows.argtypes = [P, I64, I64, P]
@@ -190,6 +192,18 @@ def vfe_step_forced(mesh, force):
         f = np.ascontiguousarray(force, dtype=np.float64)
     f = f.reshape(-1, 3)
     _check(load().vfe_step_forced(mesh, int(f.shape[0]), f.ctypes.data_as(ctypes.c_void_p)))
+
+
+def vfe_set_damping(mesh, alpha, beta):
+    _check(load().vfe_set_damping(mesh, float(alpha), float(beta)))
+
+
+def vfe_rayleigh_coefficients(h, f1_hz, f2_hz):
+    """(alpha, beta) giving damping ratio h at f1 and f2."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().vfe_rayleigh_coefficients(float(h), float(f1_hz), float(f2_hz),
+                                            ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def vfe_synchronize(mesh):
@@ -346,6 +360,9 @@ class Mesh:
 
     def step_forced(self, force):
         vfe_step_forced(self.handle, force)
+
+    def set_damping(self, alpha, beta):
+        vfe_set_damping(self.handle, alpha, beta)
 
     def synchronize(self):
         vfe_synchronize(self.handle)
