@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--stages", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--damping", type=float, default=0.0,
+                    help="Rayleigh damping ratio h over the source band (100-125 kHz on "
+                         "paper_rebar, f0 * [0.89, 1.11] otherwise); 0 = undamped")
     ap.add_argument("--trace-steps", type=int, default=2000,
                     help="length of the untimed TC vs FP64 path trace comparison "
                          "(capped by the workload's own length)")
@@ -262,9 +265,17 @@ def run_ours(args):
         ms = [a.elapsed_time(b) for a, b in ev]
         return float(np.sum(ms)), ms
 
+    def damp(mm):
+        if args.damping > 0:
+            f0 = mesh["source"]["f0"]
+            band = (100e3, 125e3) if mesh["name"].startswith("paper_rebar") else (0.89 * f0, 1.11 * f0)
+            alpha, beta = vfe.vfe_rayleigh_coefficients(args.damping, *band)
+            mm.set_damping(alpha, beta)
+        return mm
+
     # --- the TC path (headline)
-    m = vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stages=args.stages, stream=stream.cuda_stream,
-                 device=local)
+    m = damp(vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stages=args.stages,
+                      stream=stream.cuda_stream, device=local))
     with ClockSampler(local) as clk:
         total_ms, per = timed_steps(m, args.steps, args.warmup)
     clocks = clk.summary()
@@ -277,7 +288,7 @@ def run_ours(args):
     # with that step's source-node force uploaded from page-locked host memory,
     # followed by the device-to-host read of that step's receiver row
     # (synchronous); the model itself is uploaded by vfe_create_mesh.
-    m = vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stages=args.stages, device=local)
+    m = damp(vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stages=args.stages, device=local))
     row = np.zeros((1, m.n_rec, 3))
     ntot = args.warmup + args.steps
     force = torch.empty((ntot, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -298,9 +309,12 @@ def run_ours(args):
     # --- the plain FP64 CUDA-core path on the same workload, and the trace
     # agreement of the two GPU paths over the same steps
     cfg = workload_config(mesh, args.stages, "TC (exact 11-bit integer digits on tcgen05)")
+    if args.damping > 0:
+        cfg["rayleigh_damping_ratio"] = args.damping
     if not args.no_fp64:
         nf = max(3, min(args.steps, 20))
-        mf = vfe.Mesh(mesh, path=vfe.VFE_PATH_FP64, stream=stream.cuda_stream, device=local)
+        mf = damp(vfe.Mesh(mesh, path=vfe.VFE_PATH_FP64, stream=stream.cuda_stream,
+                           device=local))
         f_ms, _ = timed_steps(mf, nf, min(args.warmup, 3))
         mf.close()
         f_value = ne * nf / (f_ms * 1e-3)
@@ -311,8 +325,8 @@ def run_ours(args):
         nt = min(int(mesh["nsteps"]), args.trace_steps)
         trs = []
         for path in (vfe.VFE_PATH_TC, vfe.VFE_PATH_FP64):
-            mp = vfe.Mesh(mesh, path=path, stages=args.stages, stream=stream.cuda_stream,
-                          device=local)
+            mp = damp(vfe.Mesh(mesh, path=path, stages=args.stages, stream=stream.cuda_stream,
+                               device=local))
             mp.step(nt)
             trs.append(mp.traces())
             mp.close()
