@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (tid == 0) {
     misc[1] = 0;
     for (int i = 0; i < kUSlots; ++i) mbar_init(&bars[i], 1);
-    mbar_init(&bars[8], 2);
-    mbar_init(&bars[9], 2);
+    mbar_init(&bars[8], 4);
+    mbar_init(&bars[9], 4);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -539,11 +539,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint64_t adesc0 = make_sdesc(smem_u32(digits), 2 * kBlockBytes, kBlockBytes);
     const uint64_t bdesc0 = make_sdesc(smem_u32(bop), 6 * kBlockBytes, kBlockBytes);
     // warp t issues the MMAs of tile t (both warps are converged here)
-    // warps 8-11 (second half) issue: tile (w & 1), stages split in two parts;
-    // each commits its own MMAs to the tile's mbarrier (two arrivals)
+    // the eight warps of the second half issue (that half has slack after the
+    // barrier): tile w & 1, stages with (s - s_lo) mod 4 = (w >> 1) & 3; each
+    // commits its own MMAs to the tile's mbarrier (four arrivals)
     auto issue_mma = [&](int L) {
       const int iw = warp - TC_THREADS / 64;
-      if (iw < 0 || iw >= 4) return;
+      if (iw < 0 || iw >= 8) return;
       const int mt = iw & 1, part = iw >> 1;
       tc_fence_after();
       const int sl0 = ((L % kDigitSlots) + kDigitSlots) % kDigitSlots;
@@ -551,10 +552,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint64_t a0 = adesc0 + (uint64_t)((sl0 * kDigitSlotBytes + 16 * mt * kBlockBytes) >> 4);
       const uint64_t a1 = adesc0 + (uint64_t)((sl1 * kDigitSlotBytes + 16 * mt * kBlockBytes) >> 4);
       const uint32_t tcol = (uint32_t)(mt * kTileCols);
-      constexpr int s_mid = s_lo + (STAGES + 1) / 2;
 #pragma unroll
       for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
-        if ((s < s_mid) != (part == 0)) continue;
+        if (((s - s_lo) & 3) != part) continue;
         const uint64_t off = (uint64_t)((s * kStageBytes) >> 4);
         mma_f16_elect(tcol + (uint32_t)(s * TC_N), a0 + off, bdesc0, 0);
         mma_f16_elect(tcol + (uint32_t)(s * TC_N), a1 + off,
