@@ -309,6 +309,29 @@ __device__ __forceinline__ int64_t mul_hi63(int64_t P, int C1, int C0) {
   return r;
 }
 
+// round(S C / 2^R) for 1 <= R <= 63, S signed, 0 <= C < 2^63, from the exact
+// 128-bit product: add 2^(R-1), then the 64 bits starting at bit R
+__device__ __forceinline__ int64_t mul_shr_round(int64_t S, int64_t C, int R) {
+  int64_t r;
+  asm("{\n"
+      " .reg .u64 lo, hi, one, rnd;\n"
+      " .reg .u32 sl, sr;\n"
+      " mul.lo.u64 lo, %1, %2;\n"
+      " mul.hi.s64 hi, %1, %2;\n"
+      " sub.u32 sl, %3, 1;\n"
+      " shl.b64 rnd, 1, sl;\n"
+      " add.cc.u64 lo, lo, rnd;\n"
+      " addc.u64 hi, hi, 0;\n"
+      " shr.b64 lo, lo, %3;\n"
+      " sub.u32 sr, 64, %3;\n"
+      " shl.b64 hi, hi, sr;\n"
+      " or.b64 %0, lo, hi;\n"
+      "}\n"
+      : "=l"(r)
+      : "l"(S), "l"(C), "r"(R));
+  return r;
+}
+
 // ---------------------------------------------------------------------------
 // The fused kernel.  MODE: 0 = time step, 1 = K u only (writes S), 2 = exact
 // partial products per element (diagnostic).
@@ -766,10 +789,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               const int sh = Rseg - 63;
               du = sh == 0 ? H : (sh > 62 ? 0 : (H + ((int64_t)1 << (sh - 1))) >> sh);
             } else {
-              const __int128 prod = (__int128)S[c] * (__int128)cn;
               if (Rseg > 0) {
-                du = (int64_t)((prod + ((__int128)1 << (Rseg - 1))) >> Rseg);
+                du = mul_shr_round(S[c], cn, Rseg);
               } else {  // the state is being scaled up: exact left shift
+                const __int128 prod = (__int128)S[c] * (__int128)cn;
                 du = (int64_t)(prod << min(-Rseg, 63));
               }
             }
@@ -806,8 +829,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               or_seg |= (unsigned long long)(wn < 0 ? -wn : wn);
             }
             // the slot bounds u^{n+1} and u^n (both in the new units)
-            or_seg |= (unsigned long long)(unew[c] < 0 ? -unew[c] : unew[c]) |
-                      (unsigned long long)(uold[c] < 0 ? -uold[c] : uold[c]);
+            or_seg |= (unsigned long long)(unew[c] ^ (unew[c] >> 63)) |
+                      (unsigned long long)(uold[c] ^ (uold[c] >> 63));
           }
           if (P.trace_row >= 0)
             for (int r = 0; r < nrec; ++r) {
