@@ -169,14 +169,25 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def kernel_code_hash(path=KERNEL_SRC):
+    """First 16 hex digits of the SHA-256 of the kernel source with comments
+    and whitespace removed (so a comment edit keeps its profile)."""
+    import re
+    with open(path) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", "", src)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def profiled_counters():
     """DRAM bytes and warp instructions per launch from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    summary, if it was taken on the current kernel code (else None)."""
     try:
         with open(PROFILE_TXT) as f:
             text = f.read()
-        with open(KERNEL_SRC, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        sha = kernel_code_hash()
     except OSError:
         return None
     vals = {}
@@ -184,7 +195,7 @@ def profiled_counters():
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != sha:
+    if vals.get("kernel_code_sha256_16", "").split(" ")[0] != sha:
         return None
     try:
         return {"dram_bytes": float(vals["dram_bytes_per_launch"]),

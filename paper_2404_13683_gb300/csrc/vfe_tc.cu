@@ -553,15 +553,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const bool has_t1 = tid < ntask;
     const int src0 = task_src(t0 < 0 ? 0 : t0), dst0 = task_dst(t0 < 0 ? 0 : t0);
     const int src1 = task_src(has_t1 ? tid : 0), dst1 = task_dst(has_t1 ? tid : 0);
-    // one thread issues the MMAs of element layer L (node planes L, L+1),
-    // tile 0 first, with one commit per tile
+    // the MMAs of element layer L read digit planes L and L+1.
     // A (MN-major): 8-element chunks at 128 B, K groups (dy) at 256 B; B (K-major):
     // 8-row N groups at 128 B, K groups at 6*128 B.  Descriptors differ only in
     // the start-address field (address >> 4, below 2^14 for shared memory), so
     // they are formed by adding offsets to one base descriptor.
     const uint64_t adesc0 = make_sdesc(smem_u32(digits), 2 * kBlockBytes, kBlockBytes);
     const uint64_t bdesc0 = make_sdesc(smem_u32(bop), 6 * kBlockBytes, kBlockBytes);
-    // warp t issues the MMAs of tile t (both warps are converged here)
     // the eight warps of the second half issue (that half has slack after the
     // barrier): tile w & 1, stages with (s - s_lo) mod 4 = (w >> 1) & 3; each
     // commits its own MMAs to the tile's mbarrier (four arrivals)
