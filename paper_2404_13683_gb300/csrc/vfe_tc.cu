@@ -116,6 +116,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of a completed phase (acquire when it succeeds).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait on an mbarrier phase; false after ~2 s.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -763,8 +775,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int c = 0; c < 3; ++c) d.S_out[c * d.comp + nidx] = S[c];
         } else if (MODE == TC_MODE_STEP) {
           // plane L's slot completed its phase before half 1 digitised it; the
-          // wait returns at once and orders the TMA data before these reads
-          if (!mbar_wait(&bars[L & 7], ((uphase >> (L & 7)) & 1u) ^ 1u)) atomicExch(&misc[1], 1u);
+          // test acquires that completion for these reads
+          if (!mbar_test_wait(&bars[L & 7], ((uphase >> (L & 7)) & 1u) ^ 1u)) atomicExch(&misc[1], 1u);
           const int64_t *ucur = uslot + (L & 7) * (kUSlotStride / 8);
           const bool is_src = (nidx == d.src_node);
           // du = round(S C / 2^R): for R >= 63 (the usual case: C < 2^62 and
