@@ -60,3 +60,22 @@ def test_batch_rejects_mixed_paths():
         vfe.Batch([a, b])
     a.close()
     b.close()
+
+
+def test_batch_fewer_stages_equals_individual_runs():
+    """The batched kernel with three digit stages: bit-identical to each mesh
+    stepped alone with three stages."""
+    models = _models()[:4]
+    alone = []
+    for w in models:
+        with vfe.Mesh(w, stages=3) as m:
+            m.step(11)
+            alone.append(m.traces())
+    meshes = [vfe.Mesh(w, stages=3) for w in models]
+    with vfe.Batch(meshes) as b:
+        b.step(11)
+        b.synchronize()
+        for m, tr in zip(meshes, alone):
+            assert np.array_equal(m.traces(), tr)
+    for m in meshes:
+        m.close()

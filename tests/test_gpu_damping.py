@@ -97,3 +97,23 @@ def test_damping_rejections(orc):
         with pytest.raises(vfe.VfeError) as e:
             vfe.vfe_misfit_gradient(m.handle, data, 1)
         assert e.value.code == vfe.VFE_ESTATE
+
+
+def test_damped_tc_matches_damped_fp64_long():
+    """300 damped steps: the tensor-core path stays within its trace bar of the
+    FP64 path, with damping and a forced source together."""
+    mesh = W.random_mesh(23, shape=(40, 33, 20), void_frac=0.02)
+    out = {}
+    for path in ("tc", "fp64"):
+        with vfe.Mesh(mesh, path=PATHS[path]) as m:
+            alpha, beta = _coefficients(mesh, m.dt, h=0.05)
+            m.set_damping(alpha, beta)
+            s = mesh["source"]
+            t = np.arange(300) * m.dt
+            a = (np.pi * s["f0"] * (t - s["t0"])) ** 2
+            rows = (s["amp"] * (1 - 2 * a) * np.exp(-a))[:, None] * np.array([0.3, 0.4, 0.866])[None, :]
+            m.step_forced(rows[:150])
+            m.step_forced(rows[150:])
+            out[path] = m.traces()
+    assert np.linalg.norm(out["fp64"]) > 0
+    assert rel_l2(out["tc"], out["fp64"]) <= 1e-8
