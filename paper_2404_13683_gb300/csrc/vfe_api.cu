@@ -841,7 +841,10 @@ int vfe_step_forced(vfe_mesh *m, int n, const double *force) {
     if (cudaMalloc(&p, sizeof(double) * (3 * cap + 1)) != cudaSuccess)
       return fail(VFE_ENOMEM, "force buffer of %lld rows", (long long)cap);
     const int64_t off = -1;
-    CUDA_TRY(cudaMemcpy(p + 3 * cap, &off, sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (cudaMemcpy(p + 3 * cap, &off, sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaFree(p);
+      return fail(VFE_ECUDA, "force buffer initialisation failed");
+    }
     if (m->d_force) cudaFree(m->d_force);
     m->d_force = p;
     m->force_cap = cap;
@@ -1051,22 +1054,29 @@ int vfe_set_damping(vfe_mesh *m, double alpha, double beta) {
   int rc = vfe_get_state(m, u.data(), up.data());
   if (rc != VFE_OK) return rc;
   const bool damped = alpha > 0.0 || beta > 0.0;
-  if (damped && m->opt.path == VFE_PATH_FP64 && !m->d_w[0]) {
+  // each buffer is allocated on its own, so a failed call leaves no half-built
+  // pair behind (the next call allocates whatever is still missing)
+  if (damped && m->opt.path == VFE_PATH_FP64)
     for (int i = 0; i < 2; ++i)
-      if (cudaMalloc(&m->d_w[i], sizeof(double) * 3 * m->nn) != cudaSuccess)
+      if (!m->d_w[i] && cudaMalloc(&m->d_w[i], sizeof(double) * 3 * m->nn) != cudaSuccess) {
+        m->d_w[i] = nullptr;
         return fail(VFE_ENOMEM, "damping state");
-  }
-  if (damped && m->opt.path == VFE_PATH_TC && !m->d_W[0]) {
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled is not available");
+      }
+  if (damped && m->opt.path == VFE_PATH_TC)
     for (int i = 0; i < 2; ++i) {
-      if (cudaMalloc(&m->d_W[i], sizeof(int64_t) * 3 * m->comp) != cudaSuccess)
+      if (m->d_W[i]) continue;
+      EncodeTiledFn enc = encode_fn();
+      if (!enc) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled is not available");
+      int64_t *p = nullptr;
+      if (cudaMalloc(&p, sizeof(int64_t) * 3 * m->comp) != cudaSuccess)
         return fail(VFE_ENOMEM, "damping state");
-      CUDA_TRY(cudaMemset(m->d_W[i], 0, sizeof(int64_t) * 3 * m->comp));
-      rc = encode_state_tmap(m, enc, m->d_W[i], &m->tmap_w[i]);
-      if (rc != VFE_OK) return rc;
+      if (cudaMemset(p, 0, sizeof(int64_t) * 3 * m->comp) != cudaSuccess ||
+          (rc = encode_state_tmap(m, enc, p, &m->tmap_w[i])) != VFE_OK) {
+        cudaFree(p);
+        return rc != VFE_OK ? rc : fail(VFE_ECUDA, "damping state");
+      }
+      m->d_W[i] = p;
     }
-  }
   m->alpha = alpha;
   m->beta = beta;
   m->damped = damped;
