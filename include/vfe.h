@@ -51,7 +51,9 @@ typedef struct vfe_options {
   int path;         /* VFE_PATH_TC (default) or VFE_PATH_FP64 */
   int stages;       /* TC path: number of 11-bit integer digit stages, 1..5
                        (default 5 = 55-bit split, >= the FP64 mantissa) */
-  int fix_bottom;   /* 1 (default): every node of plane k = 0 is fixed */
+  int fix_bottom;   /* 1 (default): every node of plane k = 0 is fixed;
+                       2: the four corner nodes of plane k = 0 (Section 3);
+                       0: no node is fixed (massless nodes always are) */
   double dt;        /* time step; <= 0 selects cfl_fraction * critical step */
   double cfl_fraction; /* default 0.5 */
   int device;       /* CUDA device ordinal (default 0) */

@@ -596,6 +596,21 @@ double oracle_ricker(double t, double f0, double t0) {
   return (1.0 - 2.0 * a) * exp(-a);
 }
 
+/* ---------- fixed nodes ---------------------------------------------------- */
+
+/* fix_bottom: 0 none, 1 every node of the bottom plane k = 0, 2 the four
+ * corner nodes of the bottom plane (Section 3 fixes the four bottom corner
+ * points in x, y and z); massless nodes are always fixed. */
+static char node_fixed(int fix_bottom, int nx, int ny, int64_t n, double mass) {
+  const int64_t sx = nx + 1, sxy = (int64_t)(nx + 1) * (ny + 1);
+  const int64_t i = n % sx, j = (n / sx) % (ny + 1), k = n / sxy;
+  if (mass == 0.0) return 1;
+  if (k != 0) return 0;
+  if (fix_bottom == 1) return 1;
+  if (fix_bottom == 2) return (char)((i == 0 || i == nx) && (j == 0 || j == ny));
+  return 0;
+}
+
 int oracle_run(int kind, int nx, int ny, int nz, double ds,
                const int32_t *mat, const double *table, int n_mat,
                int fix_bottom, double dt, int nsteps,
@@ -620,8 +635,7 @@ int oracle_run(int kind, int nx, int ny, int nz, double ds,
   if (!mass || !u || !up || !un || !f || !fixed) goto done;
   if (oracle_node_mass(kind, nx, ny, nz, ds, mat, table, n_mat, mass)) goto done;
   for (int64_t n = 0; n < nn; ++n) {
-    int nk = (int)(n / ((int64_t)(nx + 1) * (ny + 1)));
-    fixed[n] = (char)((fix_bottom && nk == 0) || mass[n] == 0.0);
+    fixed[n] = node_fixed(fix_bottom, nx, ny, n, mass[n]);
   }
   for (int64_t d = 0; d < 3 * nn; ++d) {
     u[d] = u0 ? u0[d] : 0.0;
@@ -680,8 +694,7 @@ int oracle_run_damped(int kind, int nx, int ny, int nz, double ds,
   if (!mass || !u || !up || !un || !w || !f || !fixed) goto done;
   if (oracle_node_mass(kind, nx, ny, nz, ds, mat, table, n_mat, mass)) goto done;
   for (int64_t n = 0; n < nn; ++n) {
-    int nk = (int)(n / ((int64_t)(nx + 1) * (ny + 1)));
-    fixed[n] = (char)((fix_bottom && nk == 0) || mass[n] == 0.0);
+    fixed[n] = node_fixed(fix_bottom, nx, ny, n, mass[n]);
   }
   for (int64_t d = 0; d < 3 * nn; ++d) {
     u[d] = u0 ? u0[d] : 0.0;
@@ -740,8 +753,7 @@ int oracle_misfit_gradient(int kind, int nx, int ny, int nz, double ds,
   if (!U || !tr || !mass || !mu0 || !mu1 || !mu2 || !Kmu || !g || !Kg || !fixed) goto done;
   if (oracle_node_mass(kind, nx, ny, nz, ds, mat, table, n_mat, mass)) goto done;
   for (int64_t n = 0; n < nn; ++n) {
-    int nk = (int)(n / ((int64_t)(nx + 1) * (ny + 1)));
-    fixed[n] = (char)((fix_bottom && nk == 0) || mass[n] == 0.0);
+    fixed[n] = node_fixed(fix_bottom, nx, ny, n, mass[n]);
   }
   /* forward: the same run as oracle_run, keeping every state */
   for (int it = 0; it < N; ++it) {

@@ -106,6 +106,8 @@ double oracle_ricker(double t, double f0, double t0);
  * Fixed DOFs: every node of the plane k = 0 when fix_bottom, and every node
  * with zero mass.  traces[(n*n_rec + r)*3 + c] = u^{n+1} at receiver r.
  * u_out/um1_out (optional) receive u^{nsteps} and u^{nsteps-1}. */
+/* fix_bottom (here and below): 0 none, 1 the bottom plane k = 0, 2 the four
+ * corner nodes of the bottom plane (Section 3). */
 int oracle_run(int kind, int nx, int ny, int nz, double ds,
                const int32_t *mat, const double *table, int n_mat,
                int fix_bottom, double dt, int nsteps,

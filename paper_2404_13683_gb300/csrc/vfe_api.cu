@@ -385,6 +385,8 @@ int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_id
     return fail(VFE_EINVAL, "at most %d materials on the FP64 path", F64_MAX_MAT);
   if (!(opt.cfl_fraction > 0.0) || opt.cfl_fraction > 1.0)
     return fail(VFE_EINVAL, "cfl_fraction must be in (0, 1]");
+  if (opt.fix_bottom < 0 || opt.fix_bottom > 2)
+    return fail(VFE_EINVAL, "fix_bottom must be 0, 1 or 2");
 
   vfe_mesh *m = new vfe_mesh();
   m->nx = nx; m->ny = ny; m->nz = nz; m->h = h; m->opt = opt; m->device = opt.device;
@@ -428,8 +430,11 @@ int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_id
       }
   m->fixed.assign(m->nn, 0);
   for (int64_t n = 0; n < m->nn; ++n) {
+    const int64_t i = n % (nx + 1), j = (n / (nx + 1)) % (ny + 1);
     const int64_t k = n / ((int64_t)(nx + 1) * (ny + 1));
-    m->fixed[n] = (char)((opt.fix_bottom && k == 0) || m->mass[n] == 0.0);
+    const bool corner = (i == 0 || i == nx) && (j == 0 || j == ny);
+    m->fixed[n] = (char)((k == 0 && (opt.fix_bottom == 1 || (opt.fix_bottom == 2 && corner))) ||
+                         m->mass[n] == 0.0);
   }
   // critical step over the materials present
   double dtc = -1.0;

@@ -333,10 +333,12 @@ class Mesh:
     (see ``workloads.py``)."""
 
     def __init__(self, workload, path=VFE_PATH_TC, kind=VFE_OVFEM, stages=5, dt=None,
-                 fix_bottom=True, stream=None, device=0, source=True, receivers=True):
+                 fix_bottom=None, stream=None, device=0, source=True, receivers=True):
         nx, ny, nz = workload["shape"]
         if dt is None:
             dt = float(workload.get("dt", 0.0))
+        if fix_bottom is None:   # the workload's boundary condition, else the bottom plane
+            fix_bottom = workload.get("fix_bottom", 1)
         opt = vfe_default_options(element_kind=kind, path=path, stages=stages, dt=dt,
                                   fix_bottom=int(fix_bottom), device=device,
                                   stream=stream or 0)

@@ -24,7 +24,8 @@ below stand in for it:
 * ``paper_rebar``: the shape of the paper's experiment (Section 3): a
   324 x 128 x 384 mm concrete block at ds = 2 mm (162 x 64 x 192 voxels) with a
   steel rebar of radius 15 mm along y at x = 160, z = 100 mm, the source and
-  the eight observation points of Table 1, dt = 5e-8 s, 16,384 steps.  The
+  the eight observation points of Table 1, dt = 5e-8 s, 16,384 steps, the four
+  bottom corner points fixed (``fix_bottom`` = 2).  The
   paper gives no material constants; typical concrete (Vp 4000, Vs 2400,
   rho 2300) and steel (5900, 3200, 7850) values stand in.
 * ``random_mesh``: small random meshes with voids for parity tests.
@@ -174,6 +175,7 @@ def paper_rebar():
     rec = [(int(round(x / 2.0)), 30, 192) for x in (26, 60, 108, 144, 180, 216, 264, 300)]
     w = _mesh((nx, ny, nz), ds, mat, table, src, rec, 16384, "paper_rebar_162x64x192")
     w["dt"] = 5e-8
+    w["fix_bottom"] = 2   # the four bottom corner points fixed, as in the experiment
     return w
 
 

@@ -62,3 +62,17 @@ def test_config1_traces(orc, path, kind):
         m.step(mesh["nsteps"])
         tr = m.traces()
     assert rel_l2(tr, tro) <= TRACE_TOL[path]
+
+
+@pytest.mark.parametrize("path", ["tc", "fp64"])
+def test_corner_fixed_traces(orc, path):
+    """The experiment's boundary condition (the four bottom corner points
+    fixed, Section 3): traces against the oracle."""
+    mesh = W.random_mesh(44, shape=(19, 17, 9), void_frac=0.0)
+    dt = orc.dt(0, mesh, 0.5)
+    tro = orc.run(0, mesh, dt, 40, source=oracle_source(mesh), receivers=W.receiver_nodes(mesh),
+                  fix_bottom=2)
+    with vfe.Mesh(mesh, path=PATHS[path], fix_bottom=2) as m:
+        m.step(40)
+        tr = m.traces()
+    assert rel_l2(tr, tro) <= TRACE_TOL[path]
