@@ -81,6 +81,25 @@ def ricker_rows(n, dt, source):
         np.asarray(source["dir"], dtype=np.float64)[None, :]
 
 
+def paper_err(obs, ref):
+    """The paper's trace error (Section 3, accuracy comparison): the mean over
+    channels (receiver x component) of sum_t (obs - ref)^2 / sum_t ref^2,
+    over the channels whose reference is not identically zero."""
+    o = obs.reshape(obs.shape[0], -1)
+    r = ref.reshape(ref.shape[0], -1)
+    den = (r * r).sum(axis=0)
+    keep = den > 0
+    if not keep.any():
+        return None
+    return float((((o - r) ** 2).sum(axis=0)[keep] / den[keep]).mean())
+
+
+# tensor-core work per element and step: N = 48 outputs x K = 32 inputs
+# (24 data + 8 bias rows) x 2 ops per multiply-add, for each digit stage
+def tc_ops_per_element(stages):
+    return 2 * 48 * 32 * stages
+
+
 def workload_config(mesh, stages, path_name):
     nx, ny, nz = mesh["shape"]
     kind = next((v for k, v in DESCRIPTIONS.items() if mesh["name"].startswith(k)), "")
@@ -152,13 +171,16 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # roofline bookkeeping for the dominant kernel (tc_step_kernel)
 # --------------------------------------------------------------------------
-def algorithmic_bytes_per_step(mesh):
+def algorithmic_bytes_per_step(mesh, damped=False):
     """HBM bytes one time step must move at minimum: read u^n, u^{n-1} and the
     per-node update multiplier, write u^{n+1} (3 x int64 each), read each
-    element's int32 material id."""
+    element's int32 material id.  With Rayleigh damping the stiffness acts on
+    the state w^n, which is read as well and written for the next step
+    (2 x 24 bytes more per node)."""
     nx, ny, nz = mesh["shape"]
     nodes = (nx + 1) * (ny + 1) * (nz + 1)
-    return nodes * (24 + 24 + 24 + 8) + nx * ny * nz * 4
+    per_node = 24 + 24 + 24 + 8 + (48 if damped else 0)
+    return nodes * per_node + nx * ny * nz * 4
 
 
 def measured_peaks():
@@ -344,11 +366,12 @@ def run_ours(args):
         num = float(np.linalg.norm(trs[0] - trs[1]))
         den = float(np.linalg.norm(trs[1]))
         cfg["trace_rel_l2_tc_vs_fp64_path"] = num / den if den > 0 else None
+        cfg["trace_err_paper_tc_vs_fp64_path"] = paper_err(trs[0], trs[1])
         cfg["trace_steps_compared"] = nt
 
     # --- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
-    abytes = algorithmic_bytes_per_step(mesh)
+    abytes = algorithmic_bytes_per_step(mesh, damped=args.damping > 0)
     achieved = abytes / (ms_step * 1e-3) / 1e9
     prof = profiled_counters() if args.workload == "config2" else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
@@ -356,6 +379,12 @@ def run_ours(args):
             "traffic": prof["dram_bytes"] if prof else None,
             "algorithmic_bytes_per_launch": abytes, "peak_source": peak_src,
             "kernel": "tc_step_kernel (duration includes the one-thread prologue launch)"}
+    # the tensor pipe's share: fp16-digit multiply-adds per second against the
+    # measured dense bf16 rate (fp16 runs at the same rate)
+    tc_tops = tc_ops_per_element(args.stages) * ne / (ms_step * 1e-3) / 1e12
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    roof["tensor"] = {"achieved": tc_tops, "peak": tc_peak, "unit": "TFLOP/s",
+                      "frac": tc_tops / tc_peak}
     if prof:
         # the kernel is limited by instruction issue, not HBM: the same launch
         # against the GPU's warp-instruction issue rate
