@@ -1730,7 +1730,7 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
   const int nb = (N + C - 1) / C;
   vfe_mesh *adj = nullptr;
   std::vector<Snapshot> snaps(nb);
-  double *d_block = nullptr, *d_mu = nullptr, *d_grad = nullptr, *d_Kg = nullptr;
+  double *d_block = nullptr, *d_mu = nullptr, *d_grad = nullptr;
   int rc = VFE_OK;
   do {
     // the adjoint runs on a twin mesh: same geometry, materials, dt and path,
@@ -1770,20 +1770,20 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
     if (misfit_out) *misfit_out = J;
     if ((rc = rewind_mesh(adj)) != VFE_OK) break;
     if ((rc = set_injection(adj, inj.data(), N)) != VFE_OK) break;
-    // dK_e/dG at fixed kappa
-    double Kg[576];
-    element_matrix(m->opt.element_kind, m->h, -2.0 / 3.0, 1.0, Kg);
+    // dK_e/dG at fixed kappa comes from the element's closed form (alpha)
+    const double alpha = m->opt.element_kind == VFE_OVFEM ? 0.75 : 1.0 / 3.0;
     const size_t fb = sizeof(double) * 3 * m->nn;
     cudaError_t e;
     if ((e = cudaMalloc(&d_block, fb * (C + 1))) != cudaSuccess ||
         (e = cudaMalloc(&d_mu, fb)) != cudaSuccess ||
-        (e = cudaMalloc(&d_grad, sizeof(double) * m->ne)) != cudaSuccess ||
-        (e = cudaMalloc(&d_Kg, sizeof(Kg))) != cudaSuccess) {
+        (e = cudaMalloc(&d_grad, sizeof(double) * m->ne)) != cudaSuccess) {
       rc = fail(VFE_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
       break;
     }
-    CUDA_TRY(cudaMemset(d_grad, 0, sizeof(double) * m->ne));
-    CUDA_TRY(cudaMemcpy(d_Kg, Kg, sizeof(Kg), cudaMemcpyHostToDevice));
+    if ((e = cudaMemset(d_grad, 0, sizeof(double) * m->ne)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "gradient buffer: %s", cudaGetErrorString(e));
+      break;
+    }
     // backward over the blocks: recompute u^{s0..s0+len}, then adjoint steps
     for (int b = nb - 1; b >= 0 && rc == VFE_OK; --b) {
       const int s0 = b * C, len = std::min(C, N - s0);
@@ -1797,14 +1797,18 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
         if ((rc = vfe_step(adj, 1)) != VFE_OK) break;  // mu^{mi-1}
         if ((rc = state_to_f64(adj, d_mu)) != VFE_OK) break;
         const cudaError_t ge = grad_g_accumulate(
-            m->stream, m->nx, m->ny, m->nz, m->d_mat, d_Kg,
+            m->stream, m->nx, m->ny, m->nz, m->d_mat, alpha, m->h,
             d_block + (size_t)(mi - 1 - s0) * 3 * m->nn, d_mu, m->dt * m->dt, d_grad);
         if (ge != cudaSuccess) rc = fail(VFE_ECUDA, "gradient kernel: %s", cudaGetErrorString(ge));
       }
     }
     if (rc != VFE_OK) break;
     if ((rc = vfe_synchronize(adj)) != VFE_OK) break;
-    CUDA_TRY(cudaMemcpy(grad_G, d_grad, sizeof(double) * m->ne, cudaMemcpyDeviceToHost));
+    if ((e = cudaMemcpy(grad_G, d_grad, sizeof(double) * m->ne, cudaMemcpyDeviceToHost)) !=
+        cudaSuccess) {
+      rc = fail(VFE_ECUDA, "gradient read-back: %s", cudaGetErrorString(e));
+      break;
+    }
     rc = rewind_mesh(m);
   } while (0);
   std::string msg = g_last_error;
@@ -1812,7 +1816,6 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
   if (d_block) cudaFree(d_block);
   if (d_mu) cudaFree(d_mu);
   if (d_grad) cudaFree(d_grad);
-  if (d_Kg) cudaFree(d_Kg);
   if (adj) vfe_destroy(adj);
   g_last_error = msg;
   return rc;

@@ -205,9 +205,10 @@ cudaError_t tc_launch_batch_step(cudaStream_t s, const TcBatch &b, int stages);
 cudaError_t tc_state_to_f64(cudaStream_t s, const int64_t *U, const int64_t *persist,
                             int extra_shift, int nx, int ny, int64_t nn, int nxp, int64_t plane,
                             int64_t comp, double *out);
+// alpha: 3/4 for the orthogonal element, 1/3 for the trilinear one; ds: edge length
 cudaError_t grad_g_accumulate(cudaStream_t s, int nx, int ny, int nz, const int32_t *mat,
-                              const double *Kg, const double *u, const double *mu, double scale,
-                              double *grad);
+                              double alpha, double ds, const double *u, const double *mu,
+                              double scale, double *grad);
 
 size_t f64_params_bytes();
 cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,
