@@ -369,6 +369,10 @@ def run_ours(args):
         den = float(np.linalg.norm(trs[1]))
         cfg["trace_rel_l2_tc_vs_fp64_path"] = num / den if den > 0 else None
         cfg["trace_err_paper_tc_vs_fp64_path"] = paper_err(trs[0], trs[1])
+        # a record that ends before the wave reaches the receivers holds only
+        # the scheme's leading-edge tail, below the fixed-point state's quantum
+        # (2^-59 of the field maximum): the TC path records zeros there
+        cfg["trace_max_abs_fp64_path"] = float(np.abs(trs[1]).max())
         cfg["trace_steps_compared"] = nt
 
     # --- roofline of the dominant kernel
