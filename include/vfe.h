@@ -54,7 +54,9 @@ typedef struct vfe_options {
   int fix_bottom;   /* 1 (default): every node of plane k = 0 is fixed;
                        2: the four corner nodes of plane k = 0 (Section 3);
                        0: no node is fixed (massless nodes always are) */
-  double dt;        /* time step; <= 0 selects cfl_fraction * critical step */
+  double dt;        /* time step; <= 0 selects cfl_fraction * critical step;
+                       above the critical step 2/sqrt(lambda_max(M_e^-1 K_e)) of
+                       the materials present: VFE_EINVAL (the scheme diverges) */
   double cfl_fraction; /* default 0.5 */
   int device;       /* CUDA device ordinal (default 0) */
   void *stream;     /* cudaStream_t to run on; NULL = a stream the mesh owns */

@@ -451,6 +451,11 @@ int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_id
     delete m;
     return fail(VFE_EINVAL, "the mesh has no solid element");
   }
+  if (opt.dt > dtc) {  // the central-difference scheme would diverge
+    delete m;
+    return fail(VFE_EINVAL, "dt %g exceeds the stability limit %g of the materials present",
+                opt.dt, dtc);
+  }
   m->dt = opt.dt > 0.0 ? opt.dt : opt.cfl_fraction * dtc;
   m->dt_crit = dtc;
 

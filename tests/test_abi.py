@@ -46,6 +46,7 @@ def test_default_options():
     (dict(opt=dict(stages=6)), "stages"),
     (dict(opt=dict(stages=0)), "stages"),
     (dict(opt=dict(cfl_fraction=1.5)), "cfl"),
+    (dict(opt=dict(dt=1.0)), "stability limit"),
 ])
 def test_create_mesh_validation(kw, msg):
     nx = kw.get("nx", 2)
