@@ -149,6 +149,16 @@ int vfe_get_traces(vfe_mesh *mesh, double *out, int64_t *n_steps_out);
  * receiver values as they are produced.  Synchronous. */
 int vfe_get_trace_rows(vfe_mesh *mesh, int64_t first, int64_t count, double *out);
 
+/* The same copy queued on the mesh's stream behind the steps queued so far,
+ * without waiting: for streaming the receiver rows to the host while the GPU
+ * keeps stepping.  out (host, [count][n_rec][3] FP64) should be page-locked,
+ * so that the copy is asynchronous; it holds the rows once a synchronising
+ * call (vfe_synchronize, vfe_get_traces, vfe_get_trace_rows) has returned,
+ * which also reports device errors.  Rows must already be queued (first +
+ * count <= steps recorded, VFE_EINVAL otherwise); VFE_ECUDA if the copy cannot
+ * be queued. */
+int vfe_get_trace_rows_async(vfe_mesh *mesh, int64_t first, int64_t count, double *out);
+
 /* Time step in use, number of nodes, and steps taken since creation. */
 int vfe_get_dt(vfe_mesh *mesh, double *dt);
 int vfe_get_sizes(vfe_mesh *mesh, int64_t *n_nodes, int64_t *n_elements);

@@ -894,8 +894,8 @@ int vfe_get_traces(vfe_mesh *m, double *out, int64_t *n_steps_out) {
   return VFE_OK;
 }
 
-int vfe_get_trace_rows(vfe_mesh *m, int64_t first, int64_t count, double *out) {
-  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+// queue the copy of trace rows [first, first + count) on the mesh's stream
+static int enqueue_trace_rows(vfe_mesh *m, int64_t first, int64_t count, double *out) {
   if (first < 0 || count < 0 || (count > 0 && !out)) return fail(VFE_EINVAL, "bad row range");
   cudaSetDevice(m->device);
   if (first + count > m->trace_rows)
@@ -905,8 +905,20 @@ int vfe_get_trace_rows(vfe_mesh *m, int64_t first, int64_t count, double *out) {
   CUDA_TRY(cudaMemcpyAsync(out, m->d_traces + first * 3 * m->n_rec,
                            sizeof(double) * 3 * m->n_rec * count, cudaMemcpyDeviceToHost,
                            m->stream));
+  return VFE_OK;
+}
+
+int vfe_get_trace_rows(vfe_mesh *m, int64_t first, int64_t count, double *out) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  const int rc = enqueue_trace_rows(m, first, count, out);
+  if (rc != VFE_OK || count == 0 || m->n_rec == 0) return rc;
   CUDA_TRY(cudaStreamSynchronize(m->stream));
   return check_status(m);
+}
+
+int vfe_get_trace_rows_async(vfe_mesh *m, int64_t first, int64_t count, double *out) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  return enqueue_trace_rows(m, first, count, out);
 }
 
 int vfe_get_dt(vfe_mesh *m, double *dt) {

@@ -35,6 +35,7 @@ EXPORTS = (
     "vfe_get_trace_rows", "vfe_internal_force_noalloc",
     "vfe_create_batch", "vfe_batch_step", "vfe_batch_synchronize", "vfe_destroy_batch",
     "vfe_misfit_gradient", "vfe_step_forced", "vfe_set_damping", "vfe_rayleigh_coefficients",
+    "vfe_get_trace_rows_async",
 )
 
 
@@ -90,6 +91,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_synchronize.argtypes = [P]
     L.vfe_get_traces.argtypes = [P, P, ctypes.POINTER(I64)]
     L.vfe_get_trace_rows.argtypes = [P, I64, I64, P]
+    L.vfe_get_trace_rows_async.argtypes = [P, I64, I64, P]
     L.vfe_get_dt.argtypes = [P, ctypes.POINTER(D)]
     L.vfe_get_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
     L.vfe_get_step_count.argtypes = [P, ctypes.POINTER(I64)]
@@ -225,6 +227,19 @@ def vfe_get_trace_rows(mesh, first, count, n_rec, out=None):
     if out is None:
         out = np.zeros((count, n_rec, 3))
     _check(load().vfe_get_trace_rows(mesh, int(first), int(count), _p(out)))
+    return out
+
+
+def vfe_get_trace_rows_async(mesh, first, count, n_rec, out):
+    """Queue the copy of rows [first, first+count) into ``out`` (a C-contiguous
+    float64 array of at least count x n_rec x 3 values, ideally page-locked,
+    kept alive and unread until the next synchronising call)."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous):
+        raise ValueError("out must be a C-contiguous float64 array")
+    if out.size < int(count) * int(n_rec) * 3:
+        raise ValueError("out holds %d values, the rows need %d" % (out.size, count * n_rec * 3))
+    _check(load().vfe_get_trace_rows_async(mesh, int(first), int(count),
+                                           out.ctypes.data_as(ctypes.c_void_p)))
     return out
 
 

@@ -76,3 +76,31 @@ def test_forced_rejects_bad_calls():
         assert e.value.code == vfe.VFE_EINVAL
         m.step_forced(np.zeros((0, 3)))   # no steps: a no-op
         m.synchronize()
+
+
+def test_streamed_rows_equal_traces():
+    """vfe_get_trace_rows_async: each step's receiver row copied to page-locked
+    host memory behind the step, without waiting, equals the recorded traces
+    once the mesh is synchronised; the same checks on the row range as the
+    synchronous read."""
+    torch = pytest.importorskip("torch")
+    mesh = _mesh()
+    n = 30
+    with vfe.Mesh(mesh) as m:
+        out = torch.zeros((n, m.n_rec, 3), dtype=torch.float64, pin_memory=True).numpy()
+        s = mesh["source"]
+        rows = ricker_rows(n, m.dt, s["f0"], s["t0"], s["amp"], s["dir"])
+        for k in range(n):
+            if k % 2:
+                m.step(1)
+            else:
+                m.step_forced(rows[k:k + 1])
+            vfe.vfe_get_trace_rows_async(m.handle, k, 1, m.n_rec, out[k])
+        m.synchronize()
+        assert np.abs(out).max() > 0
+        assert np.array_equal(out, m.traces())
+        with pytest.raises(vfe.VfeError) as e:
+            vfe.vfe_get_trace_rows_async(m.handle, n, 1, m.n_rec, out[0])
+        assert e.value.code == vfe.VFE_EINVAL
+        with pytest.raises(ValueError):   # the host buffer is too small for two rows
+            vfe.vfe_get_trace_rows_async(m.handle, 0, 2, m.n_rec, out[0])
