@@ -574,6 +574,10 @@ def run_reference(args):
     el = time.perf_counter() - t0
     value = ne * args.steps / el
     cfg = workload_config(mesh, args.stages, "FP64 CPU oracle")
+    # the oracle runs on the host: no digit stages, no GPU cache to flush
+    for key in ("tc_digit_stages", "tc_digit_bits", "l2"):
+        cfg.pop(key, None)
+    cfg["host"] = "one thread of the host CPU, plain C (oracle/vfe_oracle.c)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
