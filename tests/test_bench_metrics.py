@@ -52,3 +52,15 @@ def test_algorithmic_bytes():
     nodes, elems = 3 * 4 * 5, 2 * 3 * 4
     assert bench.algorithmic_bytes_per_step(mesh) == 80 * nodes + 4 * elems
     assert bench.algorithmic_bytes_per_step(mesh, damped=True) == 128 * nodes + 4 * elems
+
+
+def test_paper_err_leaves_out_channels_the_wave_has_not_reached():
+    t = np.linspace(0, 1, 300)
+    ref = np.stack([np.sin(7 * t), 1e-12 * np.sin(3 * t)], axis=1)
+    obs = ref.copy()
+    obs[:, 0] *= 1.0 + 1e-4
+    obs[:, 1] = 0.0   # below the recorder's quantum: recorded as zero
+    assert bench.paper_err(obs, ref) == pytest.approx(0.5 * (1e-8 + 1.0), rel=1e-6)
+    err, n = bench.paper_err(obs, ref, rel_floor=1e-6, return_channels=True)
+    assert n == 1
+    assert err == pytest.approx(1e-8, rel=1e-6)
