@@ -84,23 +84,28 @@ int vfe_destroy(vfe_mesh *mesh);
  * Ricker wavelet (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), applied
  * as F^n at t = n dt (Section 3 uses an impulse force in z), evaluated on
  * the device each step.  t0 <= 0 selects t0 = 1/f0.  Forces at a fixed or
- * massless node are ignored. */
+ * massless node are ignored.  dir is not normalised.  Waits for the mesh's
+ * queued work.  VFE_EINVAL: node outside the grid, f0 <= 0, or a non-finite
+ * f0, t0, amp or dir component. */
 int vfe_set_source(vfe_mesh *mesh, int i, int j, int k, const double dir[3],
                    double f0_hz, double t0_s, double amp);
 
-/* Receivers at nodes ijk[n][3].  Resets the trace buffer: later vfe_step
- * calls append u^{n+1} at every receiver for every step. */
+/* Receivers at nodes ijk[n][3] (int32 i, j, k per receiver; n = 0 removes
+ * them).  Resets the trace buffer: later vfe_step calls append u^{n+1} at
+ * every receiver for every step.  Waits for the mesh's queued work.
+ * VFE_EINVAL: n < 0, ijk NULL with n > 0, or a node outside the grid. */
 int vfe_set_receivers(vfe_mesh *mesh, int n, const int32_t *ijk);
 
 /* f = K u for the whole mesh (fixed DOFs included), u and f FP64 [nodes][3]
  * host arrays.  Uses the mesh's path; does not touch the time-stepping state.
- * Synchronous. */
+ * Synchronous.  VFE_EINVAL: a NULL argument or a non-finite value in u. */
 int vfe_internal_force(vfe_mesh *mesh, const double *u, double *f);
 
 /* Advance n >= 0 central-difference steps (Eq. eqtimehistory):
  * u^{n+1} = 2u^n - u^{n-1} + dt^2 M^-1 (F^n - K u^n) on free DOFs.
  * Asynchronous on the mesh's stream (launched as a captured CUDA graph);
- * device errors surface at the next synchronising call. */
+ * device errors surface at the next synchronising call.  VFE_EINVAL: n < 0;
+ * VFE_ENOMEM: growing the device trace buffer; VFE_ECUDA: a launch failed. */
 int vfe_step(vfe_mesh *mesh, int n);
 
 /* Advance n >= 0 steps like vfe_step, with the point force at the source
@@ -165,7 +170,9 @@ int vfe_get_sizes(vfe_mesh *mesh, int64_t *n_nodes, int64_t *n_elements);
 int vfe_get_step_count(vfe_mesh *mesh, int64_t *steps);
 
 /* Read / replace the state (u^n, u^{n-1}) as FP64 [nodes][3] host arrays.
- * Values at fixed or massless nodes are forced to zero by vfe_set_state. */
+ * Values at fixed or massless nodes are forced to zero by vfe_set_state.
+ * Both wait for the mesh's queued work.  VFE_EINVAL: a NULL argument, or
+ * (vfe_set_state) a non-finite value. */
 int vfe_get_state(vfe_mesh *mesh, double *u, double *u_prev);
 int vfe_set_state(vfe_mesh *mesh, const double *u, const double *u_prev);
 

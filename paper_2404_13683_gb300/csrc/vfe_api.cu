@@ -750,8 +750,10 @@ int vfe_set_source(vfe_mesh *m, int i, int j, int k, const double dir[3], double
   if (!dir) return fail(VFE_EINVAL, "dir is NULL");
   if (i < 0 || j < 0 || k < 0 || i > m->nx || j > m->ny || k > m->nz)
     return fail(VFE_EINVAL, "source node (%d,%d,%d) outside the grid", i, j, k);
-  if (!(f0_hz > 0.0) || !std::isfinite(amp) || !std::isfinite(t0_s))
+  if (!(f0_hz > 0.0) || !std::isfinite(f0_hz) || !std::isfinite(amp) || !std::isfinite(t0_s))
     return fail(VFE_EINVAL, "need f0 > 0 and finite t0, amp");
+  if (!std::isfinite(dir[0]) || !std::isfinite(dir[1]) || !std::isfinite(dir[2]))
+    return fail(VFE_EINVAL, "dir has non-finite components");
   cudaSetDevice(m->device);
   CUDA_TRY(cudaStreamSynchronize(m->stream));
   const int64_t n = node_id(m, i, j, k);

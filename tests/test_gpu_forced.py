@@ -76,6 +76,11 @@ def test_forced_rejects_bad_calls():
         assert e.value.code == vfe.VFE_EINVAL
         m.step_forced(np.zeros((0, 3)))   # no steps: a no-op
         m.synchronize()
+        for bad_dir, f0 in (((np.nan, 0.0, 1.0), 5.0), ((0.0, np.inf, 1.0), 5.0),
+                            ((0.0, 0.0, 1.0), 0.0), ((0.0, 0.0, 1.0), np.inf)):
+            with pytest.raises(vfe.VfeError) as e:
+                vfe.vfe_set_source(m.handle, 1, 1, 1, bad_dir, f0, 0.0, 1.0)
+            assert e.value.code == vfe.VFE_EINVAL
 
 
 def test_streamed_rows_equal_traces():
