@@ -76,3 +76,42 @@ def test_workload_generators_are_seeded():
     r1, r2 = W.random_mesh(4), W.random_mesh(4)
     assert np.array_equal(r1["material_ids"], r2["material_ids"])
     assert (r1["material_ids"] >= -1).all()
+
+
+def test_every_entry_point_rejects_null_handles():
+    """Every call that takes a mesh or batch rejects NULL with VFE_EINVAL and a
+    message, before touching the GPU (destroy calls accept NULL)."""
+    import ctypes
+    lib = vfe.load()
+    d, i64, i32 = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int()
+    buf = np.zeros(64)
+    p = buf.ctypes.data_as(ctypes.c_void_p)
+    calls = {
+        "vfe_set_source": lambda: lib.vfe_set_source(None, 0, 0, 0, p, 1.0, 0.0, 1.0),
+        "vfe_set_receivers": lambda: lib.vfe_set_receivers(None, 0, None),
+        "vfe_internal_force": lambda: lib.vfe_internal_force(None, p, p),
+        "vfe_internal_force_noalloc": lambda: lib.vfe_internal_force_noalloc(None, p, p),
+        "vfe_step": lambda: lib.vfe_step(None, 1),
+        "vfe_step_forced": lambda: lib.vfe_step_forced(None, 1, p),
+        "vfe_set_damping": lambda: lib.vfe_set_damping(None, 0.0, 0.0),
+        "vfe_synchronize": lambda: lib.vfe_synchronize(None),
+        "vfe_get_traces": lambda: lib.vfe_get_traces(None, p, ctypes.byref(i64)),
+        "vfe_get_trace_rows": lambda: lib.vfe_get_trace_rows(None, 0, 1, p),
+        "vfe_get_trace_rows_async": lambda: lib.vfe_get_trace_rows_async(None, 0, 1, p),
+        "vfe_get_dt": lambda: lib.vfe_get_dt(None, ctypes.byref(d)),
+        "vfe_get_sizes": lambda: lib.vfe_get_sizes(None, ctypes.byref(i64), ctypes.byref(i64)),
+        "vfe_get_step_count": lambda: lib.vfe_get_step_count(None, ctypes.byref(i64)),
+        "vfe_get_state": lambda: lib.vfe_get_state(None, p, p),
+        "vfe_set_state": lambda: lib.vfe_set_state(None, p, p),
+        "vfe_debug_tc_partials": lambda: lib.vfe_debug_tc_partials(
+            None, p, 1, p, p, ctypes.byref(i32), ctypes.byref(i32)),
+        "vfe_misfit_gradient": lambda: lib.vfe_misfit_gradient(None, 1, p, 1, p, ctypes.byref(d)),
+        "vfe_batch_step": lambda: lib.vfe_batch_step(None, 1),
+        "vfe_batch_synchronize": lambda: lib.vfe_batch_synchronize(None),
+        "vfe_create_batch": lambda: lib.vfe_create_batch(1, None, None),
+    }
+    for name, call in calls.items():
+        assert call() == vfe.VFE_EINVAL, name
+        assert vfe.vfe_last_error(), name
+    assert lib.vfe_destroy(None) == vfe.VFE_OK
+    assert lib.vfe_destroy_batch(None) == vfe.VFE_OK
