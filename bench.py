@@ -3,8 +3,10 @@
 
 One bench "step" is one time step of the whole hot path -- f = K u over every
 element (integer-split tensor-core products) plus the central-difference
-update, source and receiver recording -- on the 128 x 128 x 64 layered model
-with 20 ellipsoidal inclusions (1,048,576 elements, ``workloads.config2``).
+update, source and receiver recording -- on the 512 x 512 x 256 model of ten
+dipping layers under a random topographic surface (67,108,864 voxels of which
+the cells above the surface are void, 67,634,433 nodes, ``workloads.config3``),
+the largest of the layered-ground workloads that fits one GPU.
 
 Prints one JSON line (rank 0).  ``value`` is element*steps/s over all ranks;
 ranks run independent replicas (the path needs no exchange on one GPU).
@@ -12,7 +14,8 @@ ranks run independent replicas (the path needs no exchange on one GPU).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 ``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
-same workload and prints the same line with ``"impl": "reference"``.
+same workload, on every host core, and prints the same line with
+``"impl": "reference"``.
 """
 from __future__ import annotations
 
@@ -32,7 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "element·steps/s, INT8-TC vs FP64 path on 1 GB300 at ≤1e-6 rel trace error"
 UNIT = "element*steps/s"
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
-PROFILE_TXT = os.path.join(ROOT, "profiles", "tc_step_kernel_config2_128x128x64.txt")
+PROFILES = {"config2": os.path.join(ROOT, "profiles", "tc_step_kernel_config2_128x128x64.txt"),
+            "config3": os.path.join(ROOT, "profiles", "tc_step_kernel_config3_512x512x256.txt")}
 KERNEL_SRC = os.path.join(ROOT, "paper_2404_13683_gb300", "csrc", "vfe_tc.cu")
 
 
@@ -51,11 +55,23 @@ def parse():
     ap.add_argument("--trace-steps", type=int, default=2000,
                     help="length of the untimed TC vs FP64 path trace comparison "
                          "(capped by the workload's own length)")
-    ap.add_argument("--workload", default="config2",
+    ap.add_argument("--workload", default="config3",
                     choices=["config2", "config3", "config4", "config5", "paper_rebar"],
-                    help="config2 (default) is the benchmark model; the others are reported "
-                         "in the design notes")
+                    help="config3 (default: 512x512x256, the largest single-GPU model) is the "
+                         "headline; config2 (128x128x64) and the others are reported in the "
+                         "design notes")
+    ap.add_argument("--shape", default=None,
+                    help="NX,NY,NZ: the config3 generator at another size (for profiling a "
+                         "smaller model of the same kind; the headline is 512,512,256)")
     return ap.parse_args()
+
+
+def make_workload(args, W):
+    if args.workload == "config3" and args.shape:
+        nx, ny, nz = (int(v) for v in args.shape.split(","))
+        return W.config3(shape=(nx, ny, nz))
+    return {"config2": W.config2, "config3": W.config3,
+            "paper_rebar": W.paper_rebar}[args.workload]()
 
 
 def dist_env():
@@ -97,6 +113,25 @@ def paper_err(obs, ref, rel_floor=0.0, return_channels=False):
         return (None, 0) if return_channels else None
     err = float((((o - r) ** 2).sum(axis=0)[keep] / den[keep]).mean())
     return (err, int(keep.sum())) if return_channels else err
+
+
+def channel_errors(obs, ref):
+    """Per-channel (receiver x component) errors of obs against ref: the
+    largest |obs - ref| relative to the channel's own peak |ref| and to the
+    strongest channel's peak, the number of channels whose reference is
+    identically zero, and the largest |obs - ref| over all channels relative
+    to the strongest peak (the bound the fixed-point state is held to)."""
+    o = obs.reshape(obs.shape[0], -1)
+    r = ref.reshape(ref.shape[0], -1)
+    d = np.abs(o - r).max(axis=0)
+    peak = np.abs(r).max(axis=0)
+    top = float(peak.max()) if peak.size else 0.0
+    live = peak > 0
+    return {"channels": int(peak.size), "zero_reference": int((~live).sum()),
+            "max_err_over_own_peak": float((d[live] / peak[live]).max()) if live.any() else None,
+            "max_err_over_strongest_peak": float(d.max() / top) if top > 0 else None,
+            "weakest_channel_peak_over_strongest": float(peak[live].min() / top)
+            if live.any() else None}
 
 
 # tensor-core work per element and step: N = 48 outputs x K = 32 inputs
@@ -208,11 +243,14 @@ def kernel_code_hash(path=KERNEL_SRC):
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
-def profiled_counters():
+def profiled_counters(workload):
     """DRAM bytes and warp instructions per launch from the committed ncu
-    summary, if it was taken on the current kernel code (else None)."""
+    summary of this workload, if it was taken on the current kernel code
+    (else None)."""
+    if workload not in PROFILES:
+        return None
     try:
-        with open(PROFILE_TXT) as f:
+        with open(PROFILES[workload]) as f:
             text = f.read()
         sha = kernel_code_hash()
     except OSError:
@@ -277,8 +315,7 @@ def run_ours(args):
         return run_batch(args, torch, dist, world, rank, local, vfe, W)
     if args.workload == "config5":
         return run_adjoint(args, torch, dist, world, rank, local, vfe, W)
-    mesh = {"config2": W.config2, "config3": W.config3,
-            "paper_rebar": W.paper_rebar}[args.workload]()
+    mesh = make_workload(args, W)
     ne = int(mesh["material_ids"].size)
     # a dedicated stream: the library launches on it and the events are
     # recorded on it (torch's default stream is the legacy NULL stream)
@@ -378,15 +415,15 @@ def run_ours(args):
         num = float(np.linalg.norm(trs[0] - trs[1]))
         den = float(np.linalg.norm(trs[1]))
         cfg["trace_rel_l2_tc_vs_fp64_path"] = num / den if den > 0 else None
-        # channels whose reference stays below 1e-6 of the strongest one
-        # (the wave has not reached them) are left out of the paper's Err
+        # the paper's Err over every channel, and over the channels whose
+        # reference peak exceeds 1e-6 of the strongest one (a channel the wave
+        # has not reached holds only the scheme's leading-edge tail)
+        cfg["trace_err_paper_all_channels"] = paper_err(trs[0], trs[1])
         err, nch = paper_err(trs[0], trs[1], rel_floor=1e-6, return_channels=True)
         cfg["trace_err_paper_tc_vs_fp64_path"] = err
         cfg["trace_err_channels"] = "%d of %d (reference peak above 1e-6 of the strongest)" % (
             nch, trs[1][0].size)
-        # a record that ends before the wave reaches the receivers holds only
-        # the scheme's leading-edge tail, below the fixed-point state's quantum
-        # (2^-59 of the field maximum): the TC path records zeros there
+        cfg["trace_channels"] = channel_errors(trs[0], trs[1])
         cfg["trace_max_abs_fp64_path"] = float(np.abs(trs[1]).max())
         cfg["trace_steps_compared"] = nt
 
@@ -394,7 +431,7 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     abytes = algorithmic_bytes_per_step(mesh, damped=args.damping > 0)
     achieved = abytes / (ms_step * 1e-3) / 1e9
-    prof = profiled_counters() if args.workload == "config2" else None
+    prof = profiled_counters(args.workload) if args.damping == 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
             "frac": achieved / float(peaks["hbm_gbs"]),
             "traffic": prof["dram_bytes"] if prof else None,
@@ -417,7 +454,7 @@ def run_ours(args):
     # --- the CPU oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(mesh, target_s=15.0)
+        cpu = cpu_baseline(mesh)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -534,66 +571,92 @@ def run_adjoint(args, torch, dist, world, rank, local, vfe, W):
 # --------------------------------------------------------------------------
 # the CPU oracle (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------
-def _oracle_step_runner(mesh):
+def _oracle_runner(mesh, threads):
+    """A function n -> seconds that runs the FP64 CPU oracle n time steps of
+    the workload from rest (source, receivers and fixed nodes as the GPU runs
+    use them) on the given number of threads, and the threads in effect."""
     import oracle
     from paper_2404_13683_gb300 import workloads as W
     oracle.build()
-    dt = oracle.dt(0, mesh, 0.5)
+    used = oracle.set_threads(threads)
+    dt = float(mesh["dt"]) if "dt" in mesh else oracle.dt(0, mesh, 0.5)
     s = mesh["source"]
     src = {"node": W.source_node(mesh), "dir": s["dir"], "f0": s["f0"], "t0": s["t0"],
            "amp": s["amp"]}
     rec = W.receiver_nodes(mesh)
-    nn = (mesh["shape"][0] + 1) * (mesh["shape"][1] + 1) * (mesh["shape"][2] + 1)
-    state = {"u": np.zeros(3 * nn), "um": np.zeros(3 * nn)}
+    fix = int(mesh.get("fix_bottom", 1))
 
-    def step(n):
-        _, u, um = oracle.run(0, mesh, dt, n, source=src, receivers=rec, u0=state["u"],
-                              um1=state["um"], return_state=True)
-        state["u"], state["um"] = u, um
-    return step
+    def run(n):
+        oracle.set_threads(used)
+        t0 = time.perf_counter()
+        oracle.run(0, mesh, dt, n, source=src, receivers=rec, fix_bottom=fix)
+        return time.perf_counter() - t0
+    return run, used
 
 
-def cpu_baseline(mesh, target_s=15.0):
-    step = _oracle_step_runner(mesh)
+def _oracle_rate(run, ne, target_s):
+    """element*steps/s of the oracle over about target_s seconds of steps,
+    and the steps timed.  A run of 0 steps (allocation, node masses, fixed
+    nodes) is timed too and subtracted, so only the time steps count."""
+    setup = run(0)
+    one = max(run(1) - setup, 1e-3)
+    n = max(1, int(round(target_s / one)))
+    el = run(n) - setup
+    return ne * n / max(el, 1e-9), n
+
+
+def cpu_baseline(mesh, target_s=12.0):
+    """The oracle on every host core (the value) and on one core, each on a
+    bounded sample of whole time steps of the workload."""
+    import oracle
     ne = int(mesh["material_ids"].size)
-    t0 = time.perf_counter()
-    step(1)
-    one = time.perf_counter() - t0
-    n = max(1, int(target_s / max(one, 1e-3)))
-    t0 = time.perf_counter()
-    step(n)
-    el = time.perf_counter() - t0
-    return {"value": ne * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d time steps of the full %s model (element-by-element FP64 K u and "
-                      "update, plain C, one thread)" % (n, mesh["name"])}
+    run_all, cores = _oracle_runner(mesh, oracle.host_cores())
+    v_all, n_all = _oracle_rate(run_all, ne, target_s)
+    run_one, _ = _oracle_runner(mesh, 1)
+    v_one, n_one = _oracle_rate(run_one, ne, 0.0)
+    oracle.set_threads(1)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": oracle.cpu_model(),
+            "sample": "%d time steps of the full %s model from rest (element-by-element FP64 "
+                      "K u in eight colours of element parity, and the update, plain C with "
+                      "OpenMP on %d threads); setup (allocation, node masses) excluded"
+                      % (n_all, mesh["name"], cores),
+            "single_thread": {"value": v_one, "cores": 1,
+                              "sample": "%d time step(s), the plain sequential element loop"
+                                        % n_one}}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    import oracle
     from paper_2404_13683_gb300 import workloads as W
-    mesh = W.config2()
+    if args.workload not in ("config2", "config3", "paper_rebar"):
+        args.workload = "config3"
+    mesh = make_workload(args, W)
     ne = int(mesh["material_ids"].size)
-    step = _oracle_step_runner(mesh)
-    for _ in range(args.warmup):
-        step(1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step(1)
-    el = time.perf_counter() - t0
+    run, cores = _oracle_runner(mesh, oracle.host_cores())
+    setup = run(0)
+    if args.warmup > 0:
+        run(args.warmup)
+    el = run(args.steps) - setup
     value = ne * args.steps / el
     cfg = workload_config(mesh, args.stages, "FP64 CPU oracle")
     # the oracle runs on the host: no digit stages, no GPU cache to flush
     for key in ("tc_digit_stages", "tc_digit_bits", "l2"):
         cfg.pop(key, None)
-    cfg["host"] = "one thread of the host CPU, plain C (oracle/vfe_oracle.c)"
+    cfg["host"] = "%d threads of the host CPU (%s), plain C with OpenMP (oracle/vfe_oracle.c)" % (
+        cores, oracle.cpu_model())
+    sample = ("%d time steps of the full %s model from rest, timed as one oracle run; its "
+              "setup (allocation, node masses), timed by a run of 0 steps, is subtracted"
+              % (args.steps, mesh["name"]))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step = one full time step of %s" % mesh["name"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

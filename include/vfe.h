@@ -91,13 +91,20 @@ int vfe_set_source(vfe_mesh *mesh, int i, int j, int k, const double dir[3],
                    double f0_hz, double t0_s, double amp);
 
 /* Receivers at nodes ijk[n][3] (int32 i, j, k per receiver; n = 0 removes
- * them).  Resets the trace buffer: later vfe_step calls append u^{n+1} at
+ * them): the observation points of Section 3, whose displacement histories
+ * the paper compares (Table 1 lists its source and observation points).
+ * Resets the trace buffer: later vfe_step calls append u^{n+1} at
  * every receiver for every step.  Waits for the mesh's queued work.
  * VFE_EINVAL: n < 0, ijk NULL with n > 0, or a node outside the grid. */
 int vfe_set_receivers(vfe_mesh *mesh, int n, const int32_t *ijk);
 
 /* f = K u for the whole mesh (fixed DOFs included), u and f FP64 [nodes][3]
- * host arrays.  Uses the mesh's path; does not touch the time-stepping state.
+ * host arrays: the element-by-element internal force of Eq. DGE:ORG, with
+ * K_e of Eq. OVFEMstiff (OVFEM) or of the trilinear element (VFEM).  On the
+ * tensor-core path K_e u_e is formed as in Eq. GE:TC from the integer split
+ * of Eqs. intscaling and int8comp1-int8comp2, recombined exactly (an integer
+ * split of 55 bits, at least the FP64 mantissa, with the default stages).
+ * Uses the mesh's path; does not touch the time-stepping state.
  * Synchronous.  VFE_EINVAL: a NULL argument or a non-finite value in u. */
 int vfe_internal_force(vfe_mesh *mesh, const double *u, double *f);
 
@@ -146,7 +153,10 @@ int vfe_rayleigh_coefficients(double h, double f1_hz, double f2_hz, double *alph
 int vfe_synchronize(vfe_mesh *mesh);
 
 /* Copy the traces recorded since vfe_set_receivers: out[s][r][3] FP64 for
- * s < *n_steps_out (out may be NULL to query the count only).  Synchronous. */
+ * s < *n_steps_out (out may be NULL to query the count only): the time
+ * histories of displacement at the observation points that Section 3
+ * compares between the methods (its Err is computed from them).  Row s is
+ * u^{s+1} after step s.  Synchronous. */
 int vfe_get_traces(vfe_mesh *mesh, double *out, int64_t *n_steps_out);
 
 /* Copy trace rows [first, first+count) (same layout as vfe_get_traces) after
@@ -188,6 +198,15 @@ const char *vfe_last_error(void);
 int vfe_debug_tc_partials(vfe_mesh *mesh, const double *u, int n,
                           const int64_t *ids, int64_t *out, int *shift_out,
                           int *frac_bits_out);
+
+/* Test hook for the error paths: ORs bits (1 wait timeout, 2 fixed-point
+ * shift out of range, 4 tensor-memory allocation failure, 8 forced step past
+ * the supplied rows) into the mesh's device status word, as the kernels do
+ * when such a failure happens, so that tests can check that every call which
+ * reads the word reports it, without making a GPU fault or wait.  The word
+ * is sticky: the mesh keeps reporting the error until it is destroyed.
+ * Waits for the mesh's queued work.  The paper has no counterpart. */
+int vfe_debug_inject_status(vfe_mesh *mesh, int bits);
 
 /* Adjoint-state gradient (the paper's internal-structure estimation use,
  * Section 1).  For a run of nsteps from rest with the mesh's source and the

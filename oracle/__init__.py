@@ -25,14 +25,52 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``liboracle.so`` with gcc (plain C, -O2, no architecture flags)."""
+    """Compile ``liboracle.so`` with gcc (plain C, -O2, no architecture flags;
+    OpenMP for the optional multi-threaded loops, dropped if the compiler
+    lacks it)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "vfe_oracle.h"))):
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:5] + ["-fopenmp"] + base[5:],
+                                  stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def host_cores() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo; '' if unknown)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":", 1)[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def set_threads(n: int) -> int:
+    """Threads for the element loop of ``ku`` and the runs (see
+    ``oracle_set_threads`` in vfe_oracle.h); returns the count in effect."""
+    return int(lib().oracle_set_threads(int(n)))
+
+
+def get_threads() -> int:
+    return int(lib().oracle_get_threads())
 
 
 def lib() -> ctypes.CDLL:
@@ -60,6 +98,10 @@ def lib() -> ctypes.CDLL:
                                  i, p, p, p, p, p, p]
         L.oracle_run_damped.argtypes = [i, i, i, i, d, p, p, i, i, d, i, i64, p, d, d, d, d, d,
                                         i, p, p, p, p, p, p]
+        L.oracle_set_threads.argtypes = [i]
+        L.oracle_set_threads.restype = i
+        L.oracle_get_threads.argtypes = []
+        L.oracle_get_threads.restype = i
         L.oracle_misfit_gradient.argtypes = [i, i, i, i, d, p, p, i, i, d, i, i64, p, d, d, d,
                                              i, p, p, p, p]
         _lib = L

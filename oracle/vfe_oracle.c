@@ -446,6 +446,44 @@ int oracle_node_mass(int kind, int nx, int ny, int nz, double ds,
   return 0;
 }
 
+/* K_e u_e of element (i,j,k) with material m (FP64 K_e, or Eq. GE:TC with
+ * the M-stage integer expansion when tc_stages > 0), and its 8 node ids. */
+static int element_ku(int nx, int ny, int i, int j, int k, int m, double ds,
+                      const double *Km, const double *kap, const double *gg,
+                      int tc_stages, const double *u, int64_t nodes[8],
+                      double fe[24]) {
+  double ue[24];
+  for (int a = 0; a < 8; ++a) {
+    nodes[a] = node_id(nx, ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    for (int c = 0; c < 3; ++c) ue[3 * a + c] = u[3 * nodes[a] + c];
+  }
+  if (tc_stages > 0)
+    return oracle_ku_element_tc_int(ds, kap[m], gg[m], tc_stages, ue, fe);
+  const double *K = Km + 576 * m;
+  for (int r = 0; r < 24; ++r) {
+    double acc = 0.0;
+    for (int s = 0; s < 24; ++s) acc += K[r * 24 + s] * ue[s];
+    fe[r] = acc;
+  }
+  return 0;
+}
+
+/* Threads used by the element loop of oracle_ku and the update loops of the
+ * runs (1 = the plain sequential loops). */
+static int g_threads = 1;
+
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  g_threads = n < 1 ? 1 : n;
+#else
+  g_threads = 1;
+  (void)n;
+#endif
+  return g_threads;
+}
+
+int oracle_get_threads(void) { return g_threads; }
+
 int oracle_ku(int kind, int nx, int ny, int nz, double ds,
               const int32_t *mat, const double *table, int n_mat,
               int tc_stages, const double *u, double *f) {
@@ -458,34 +496,54 @@ int oracle_ku(int kind, int nx, int ny, int nz, double ds,
   if (!Km || !kap || !gg) { free(Km); free(kap); free(gg); return -1; }
   int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   for (int64_t d = 0; d < 3 * nn; ++d) f[d] = 0.0;
-  for (int k = 0; k < nz; ++k)
-    for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        int32_t m = mat[i + (int64_t)nx * (j + (int64_t)ny * k)];
-        if (m < 0) continue;
-        int64_t nodes[8];
-        double ue[24], fe[24];
-        for (int a = 0; a < 8; ++a) {
-          nodes[a] = node_id(nx, ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
-          for (int c = 0; c < 3; ++c) ue[3 * a + c] = u[3 * nodes[a] + c];
-        }
-        if (tc_stages > 0) {
-          if (oracle_ku_element_tc_int(ds, kap[m], gg[m], tc_stages, ue, fe)) {
-            free(Km); free(kap); free(gg); return -1;
+  int bad = 0;
+  if (g_threads <= 1) {
+    /* f = sum_e P_e^T K_e P_e u in element order */
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          int32_t m = mat[i + (int64_t)nx * (j + (int64_t)ny * k)];
+          if (m < 0) continue;
+          int64_t nodes[8];
+          double fe[24];
+          if (element_ku(nx, ny, i, j, k, m, ds, Km, kap, gg, tc_stages, u, nodes, fe)) {
+            bad = 1;
+            continue;
           }
-        } else {
-          const double *K = Km + 576 * m;
-          for (int r = 0; r < 24; ++r) {
-            double acc = 0.0;
-            for (int s = 0; s < 24; ++s) acc += K[r * 24 + s] * ue[s];
-            fe[r] = acc;
+          for (int a = 0; a < 8; ++a)
+            for (int c = 0; c < 3; ++c) f[3 * nodes[a] + c] += fe[3 * a + c];
+        }
+  } else {
+    /* The same sum over elements in eight colours (i, j, k parities): two
+     * elements of one colour share no node, so each colour's elements are
+     * added in parallel without races.  Only the order in which a node's
+     * (at most eight) contributions are added differs from the loop above. */
+    for (int color = 0; color < 8; ++color) {
+      const int ci = color & 1, cj = (color >> 1) & 1, ck = color >> 2;
+      const int mz = (nz - ck + 1) / 2, my = (ny - cj + 1) / 2;
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(static) num_threads(g_threads) reduction(|| : bad)
+#endif
+      for (int kk = 0; kk < mz; ++kk)
+        for (int jj = 0; jj < my; ++jj) {
+          const int k = ck + 2 * kk, j = cj + 2 * jj;
+          for (int i = ci; i < nx; i += 2) {
+            int32_t m = mat[i + (int64_t)nx * (j + (int64_t)ny * k)];
+            if (m < 0) continue;
+            int64_t nodes[8];
+            double fe[24];
+            if (element_ku(nx, ny, i, j, k, m, ds, Km, kap, gg, tc_stages, u, nodes, fe)) {
+              bad = 1;
+              continue;
+            }
+            for (int a = 0; a < 8; ++a)
+              for (int c = 0; c < 3; ++c) f[3 * nodes[a] + c] += fe[3 * a + c];
           }
         }
-        for (int a = 0; a < 8; ++a)
-          for (int c = 0; c < 3; ++c) f[3 * nodes[a] + c] += fe[3 * a + c];
-      }
+    }
+  }
   free(Km); free(kap); free(gg);
-  return 0;
+  return bad ? -1 : 0;
 }
 
 int oracle_ku_nodes(int kind, int nx, int ny, int nz, double ds,
@@ -645,6 +703,9 @@ int oracle_run(int kind, int nx, int ny, int nz, double ds,
   for (int it = 0; it < nsteps; ++it) {
     if (oracle_ku(kind, nx, ny, nz, ds, mat, table, n_mat, 0, u, f)) goto done;
     double fsrc = src_node >= 0 ? amp * oracle_ricker(it * dt, f0, t0) : 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
+#endif
     for (int64_t n = 0; n < nn; ++n)
       for (int c = 0; c < 3; ++c) {
         int64_t d = 3 * n + c;

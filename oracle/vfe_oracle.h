@@ -79,6 +79,15 @@ int oracle_ku(int kind, int nx, int ny, int nz, double ds,
               const int32_t *mat, const double *table, int n_mat,
               int tc_stages, const double *u, double *f);
 
+/* Threads for oracle_ku's element loop and the runs' update loops (built
+ * with OpenMP; 1 thread otherwise).  With n > 1 the elements are visited in
+ * eight colours of (i, j, k) parity, so that no two elements summed at the
+ * same time share a node; each element's K_e u_e is the same arithmetic as
+ * with one thread, and only the order of the at most eight additions into a
+ * node differs.  Returns the count in effect (default 1). */
+int oracle_set_threads(int n);
+int oracle_get_threads(void);
+
 /* Same as oracle_ku but only for the listed nodes: f_sel[3*q+c] is the
  * force at node sel[q].  Used to check sampled outputs of large meshes. */
 int oracle_ku_nodes(int kind, int nx, int ny, int nz, double ds,

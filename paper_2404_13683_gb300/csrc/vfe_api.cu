@@ -314,6 +314,7 @@ static int check_status(vfe_mesh *m) {
   CUDA_TRY(cudaMemcpy(&st, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st & 1) return fail(VFE_ETIMEOUT, "a device-side wait timed out (status %d)", st);
   if (st & 2) return fail(VFE_ETIMEOUT, "fixed-point shift out of range (status %d)", st);
+  if (st & 4) return fail(VFE_ECUDA, "tensor-memory allocation failed (status %d)", st);
   if (st & 8) return fail(VFE_ESTATE, "a forced step ran past the supplied force rows (status %d)", st);
   return VFE_OK;
 }
@@ -1255,6 +1256,7 @@ int vfe_internal_force(vfe_mesh *m, const double *u, double *f) {
   } while (0);
   if (du) cudaFree(du);
   if (df) cudaFree(df);
+  if (rc == VFE_OK) rc = check_status(m);  // a failure flagged by earlier work
   return rc;
 }
 
@@ -1287,6 +1289,18 @@ CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v
 }
 
 extern "C" {
+
+int vfe_debug_inject_status(vfe_mesh *m, int bits) {
+  if (!m) return fail(VFE_EINVAL, "NULL mesh");
+  if (bits & ~15) return fail(VFE_EINVAL, "status bits outside 1, 2, 4, 8");
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  int st = 0;
+  CUDA_TRY(cudaMemcpy(&st, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  st |= bits;
+  CUDA_TRY(cudaMemcpy(m->d_status, &st, sizeof(int), cudaMemcpyHostToDevice));
+  return VFE_OK;
+}
 
 int vfe_debug_tc_partials(vfe_mesh *m, const double *u, int n, const int64_t *ids, int64_t *out,
                           int *shift_out, int *frac_bits_out) {

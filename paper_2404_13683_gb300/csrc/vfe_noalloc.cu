@@ -20,6 +20,7 @@
 // it: everything that must start at zero is cleared by each call, and calls
 // whose work overlaps on a GPU (other threads, other streams) race on it.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 
@@ -112,6 +113,17 @@ __global__ void noalloc_from_fixed_kernel(const int64_t *S, int nx, int ny, int6
     }                                                                                       \
   } while (0)
 
+// Puts the caller's current device back when the call returns.
+struct DeviceRestore {
+  int prev = -1;
+  DeviceRestore() {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  }
+  ~DeviceRestore() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 // the device address of the array on the current device (set up once)
 int scratch_address(int device, unsigned char **out) {
   if (device < 0 || device >= kMaxDevices) return set_err(VFE_EINVAL, "device ordinal out of range");
@@ -140,6 +152,9 @@ int vfe_internal_force_noalloc(vfe_mesh *mesh, const double *u, double *f) {
   VfeMeshView v;
   if (vfe_mesh_view(mesh, &v) != VFE_OK) return set_err(VFE_EINVAL, "bad mesh");
   if (!v.tc) return set_err(VFE_ESTATE, "the no-alloc K u needs a mesh on the tensor-core path");
+  // a NaN or an infinity would make the fixed-point scale meaningless
+  for (int64_t i = 0; i < 3 * v.nn; ++i)
+    if (!std::isfinite(u[i])) return set_err(VFE_EINVAL, "u has non-finite values");
   const size_t region = sizeof(int64_t) * 3 * (size_t)v.comp;
   const size_t need = kHeader + 2 * region;
   if (need > (size_t)VFE_NOALLOC_SCRATCH_BYTES) {
@@ -149,6 +164,7 @@ int vfe_internal_force_noalloc(vfe_mesh *mesh, const double *u, double *f) {
              need, (size_t)VFE_NOALLOC_SCRATCH_BYTES);
     return set_err(VFE_EINVAL, m);
   }
+  DeviceRestore restore;
   NA_TRY(cudaSetDevice(v.device));
   unsigned char *base = nullptr;
   int rc = scratch_address(v.device, &base);
@@ -192,6 +208,27 @@ int vfe_internal_force_noalloc(vfe_mesh *mesh, const double *u, double *f) {
   NA_TRY(cudaGetLastError());
   NA_TRY(cudaMemcpyAsync(f, regA, sizeof(double) * n3, cudaMemcpyDeviceToHost, s));
   NA_TRY(cudaStreamSynchronize(s));
+  // the kernel's status word: a bounded wait that gave up, or a failed
+  // tensor-memory allocation, leaves f unwritten (read like vfe_internal_force)
+  int st = 0;
+  NA_TRY(cudaMemcpy(&st, v.dev.status, sizeof(int), cudaMemcpyDeviceToHost));
+  char m[128];
+  if (st & 1) {
+    snprintf(m, sizeof(m), "a device-side wait timed out (status %d)", st);
+    return set_err(VFE_ETIMEOUT, m);
+  }
+  if (st & 2) {
+    snprintf(m, sizeof(m), "fixed-point shift out of range (status %d)", st);
+    return set_err(VFE_ETIMEOUT, m);
+  }
+  if (st & 4) {
+    snprintf(m, sizeof(m), "tensor-memory allocation failed (status %d)", st);
+    return set_err(VFE_ECUDA, m);
+  }
+  if (st & 8) {
+    snprintf(m, sizeof(m), "a forced step ran past the supplied force rows (status %d)", st);
+    return set_err(VFE_ESTATE, m);
+  }
   return VFE_OK;
 }
 

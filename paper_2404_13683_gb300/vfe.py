@@ -35,7 +35,7 @@ EXPORTS = (
     "vfe_get_trace_rows", "vfe_internal_force_noalloc",
     "vfe_create_batch", "vfe_batch_step", "vfe_batch_synchronize", "vfe_destroy_batch",
     "vfe_misfit_gradient", "vfe_step_forced", "vfe_set_damping", "vfe_rayleigh_coefficients",
-    "vfe_get_trace_rows_async",
+    "vfe_get_trace_rows_async", "vfe_debug_inject_status",
 )
 
 
@@ -100,6 +100,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_last_error.argtypes = []
     L.vfe_last_error.restype = ctypes.c_char_p
     L.vfe_debug_tc_partials.argtypes = [P, P, I, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    L.vfe_debug_inject_status.argtypes = [P, I]
     for name in EXPORTS:
         if name not in ("vfe_default_options", "vfe_last_error"):
             getattr(L, name).restype = ctypes.c_int

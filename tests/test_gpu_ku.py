@@ -85,3 +85,21 @@ def test_ku_full_size_sampled(orc):
             t = np.zeros(3 * nn); t[2::3] = 1e-3
             ft = m.internal_force(t)
             assert np.abs(ft).max() <= 1e-12 * np.abs(f).max() * 1e3, path
+
+
+@pytest.mark.parametrize("path", ["tc", "fp64"])
+@pytest.mark.parametrize("bit,code", [(1, vfe.VFE_ETIMEOUT), (2, vfe.VFE_ETIMEOUT),
+                                      (4, vfe.VFE_ECUDA)])
+def test_status_word_is_reported(path, bit, code):
+    """A failure flagged on the device (injected from the host here, as a
+    kernel flags a bounded wait that gave up) fails the calls that read it."""
+    mesh = W.random_mesh(61, shape=(6, 5, 4), void_frac=0.0)
+    with vfe.Mesh(mesh, path=PATHS[path], source=False, receivers=False) as m:
+        assert vfe.load().vfe_debug_inject_status(m.handle, bit) == vfe.VFE_OK
+        with pytest.raises(vfe.VfeError) as e:
+            m.internal_force(W.random_displacement(mesh, 1))
+        assert e.value.code == code
+        m.step(1)
+        with pytest.raises(vfe.VfeError) as e:
+            m.synchronize()
+        assert e.value.code == code

@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
 
 def test_replica_reduction_world2():
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.start_processes(_worker, args=(2, port, out), nprocs=2, start_method="spawn")
     assert out[0][0] == out[1][0] == 2.25
