@@ -60,6 +60,12 @@ typedef struct vfe_options {
   double cfl_fraction; /* default 0.5 */
   int device;       /* CUDA device ordinal (default 0) */
   void *stream;     /* cudaStream_t to run on; NULL = a stream the mesh owns */
+  int stencil;      /* TC path: 1 (default) forms K u on node planes whose
+                       surrounding elements share one material as one node
+                       stencil per material part (the element products of
+                       Eq. GE:TC summed at the node, same integer split); 0
+                       uses the element-by-element kernel everywhere.  The two
+                       agree to the FP64-equivalent bound of the split. */
 } vfe_options;
 
 typedef struct vfe_mesh vfe_mesh;
@@ -198,6 +204,18 @@ const char *vfe_last_error(void);
 int vfe_debug_tc_partials(vfe_mesh *mesh, const double *u, int n,
                           const int64_t *ids, int64_t *out, int *shift_out,
                           int *frac_bits_out);
+
+/* Exact integer partial sums of the node-stencil kernel: for u (FP64
+ * [nodes][3], host) digitised as the kernel does (q = floor(U / 2^shift) of
+ * the fixed-point state U = round(u 2^frac_bits)), out[node][9] int64 holds
+ * P = S^k q, the stencil part S^G q of Q, and q' (the node's own q as its
+ * kept digits give it) for every node the node-stencil kernel owns, where
+ * covered[node] = 1; 0 elsewhere.  S^k and S^G are the node sums of the
+ * integer matrices of Eq. GE:TC (K^kappa and the paper's Kbar^G) over the
+ * node's eight elements.  Diagnostic: lets tests check the tensor-core
+ * arithmetic of that kernel bit for bit.  TC path only; synchronous. */
+int vfe_debug_stencil_partials(vfe_mesh *mesh, const double *u, int64_t *out,
+                               int8_t *covered, int *shift_out, int *frac_bits_out);
 
 /* Test hook for the error paths: ORs bits (1 wait timeout, 2 fixed-point
  * shift out of range, 4 tensor-memory allocation failure, 8 forced step past

@@ -175,10 +175,24 @@ struct vfe_mesh {
   int64_t *d_tcpersist = nullptr;
   CUtensorMap tmap[2];
   int tiles_x = 0, tiles_y = 0, n_ctas = 0;
-  std::vector<int4> segs;         // (tile x, tile y, z0, z1)
+  std::vector<int4> segs;         // element kernel: (tile x, tile y, z0, z1)
   std::vector<int32_t> seg_off;   // CTA -> first segment
   int4 *d_segs = nullptr;
   int32_t *d_seg_off = nullptr;
+  // every column-plane on the element kernel (its exact-partials mode)
+  int4 *d_all_segs = nullptr;
+  int32_t *d_all_off = nullptr;
+  int all_ctas = 0;
+  // node-stencil kernel on the uniform runs (stencil_on): its segments, their
+  // material, its CTA ranges, its B image and its tensor maps (box 20x18x1x3)
+  bool stencil_on = false;
+  std::vector<int4> st_segs;
+  std::vector<int32_t> st_mat, st_off;
+  int st_ctas = 0;
+  int4 *d_st_segs = nullptr;
+  int32_t *d_st_mat = nullptr, *d_st_off = nullptr;
+  uint16_t *d_Bst = nullptr;
+  CUtensorMap st_tmap[2];
   int e_ref = 0, eC = 0;
   double src_scale = 0.0;  // dt^2 / m at the source node
 
@@ -240,6 +254,21 @@ static TcDevice tc_device(const vfe_mesh *m, int cur) {
   return d;
 }
 
+// the same arguments for the node-stencil kernel over the uniform runs
+static TcDevice tc_stencil_device(const vfe_mesh *m, int cur) {
+  TcDevice d = tc_device(m, cur);
+  d.segs = m->d_st_segs;
+  d.seg_off = m->d_st_off;
+  d.seg_mat = m->d_st_mat;
+  d.n_ctas = m->stencil_on ? m->st_ctas : 0;
+  d.Bst = m->d_Bst;
+  d.recv = nullptr;
+  d.recv_off = nullptr;
+  d.n_rec = 0;
+  d.src_node = -1;
+  return d;
+}
+
 static F64Device f64_device(const vfe_mesh *m, int cur) {
   F64Device d;
   memset(&d, 0, sizeof(d));
@@ -276,8 +305,13 @@ static int enqueue_step(vfe_mesh *m, int cur) {
                                    m->tiles_x * m->tiles_y, m->has_src ? 1 : 0, trace_on,
                                    m->d_status, m->d_inj, 3 * m->n_rec));
     TcDevice d = tc_device(m, cur);
-    CUDA_TRY(tc_launch_step(m->stream, d, m->damped ? &m->tmap_w[cur] : &m->tmap[cur],
-                            TC_MODE_STEP));
+    if (d.n_ctas > 0)
+      CUDA_TRY(tc_launch_step(m->stream, d, m->damped ? &m->tmap_w[cur] : &m->tmap[cur],
+                              TC_MODE_STEP));
+    if (m->stencil_on) {
+      TcDevice ds = tc_stencil_device(m, cur);
+      CUDA_TRY(stencil_launch(m->stream, ds, &m->st_tmap[cur], TC_MODE_STEP));
+    }
   } else {
     src.amp_scale = m->amp;
     src.force_scale = 1.0;
@@ -335,6 +369,7 @@ void vfe_default_options(vfe_options *o) {
   o->cfl_fraction = 0.5;
   o->device = 0;
   o->stream = nullptr;
+  o->stencil = 1;
 }
 
 int vfe_destroy(vfe_mesh *m) {
@@ -347,7 +382,8 @@ int vfe_destroy(vfe_mesh *m) {
                   m->d_U[0], m->d_U[1], m->d_C, m->d_Bop, m->d_mats, m->d_recv,
                   m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist, m->d_segs,
                   m->d_seg_off, m->d_inj, m->d_force, m->d_w[0], m->d_w[1],
-                  m->d_W[0], m->d_W[1]};
+                  m->d_W[0], m->d_W[1], m->d_all_segs, m->d_all_off, m->d_st_segs,
+                  m->d_st_mat, m->d_st_off, m->d_Bst};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -358,6 +394,7 @@ int vfe_destroy(vfe_mesh *m) {
 static int build_tc(vfe_mesh *m);
 static int build_f64(vfe_mesh *m);
 static int rebuild_receivers(vfe_mesh *m);
+static int rebuild_work(vfe_mesh *m);
 
 int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_ids,
                     const double *material_table, int n_materials, const vfe_options *opt_in,
@@ -389,6 +426,7 @@ int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_id
     return fail(VFE_EINVAL, "cfl_fraction must be in (0, 1]");
   if (opt.fix_bottom < 0 || opt.fix_bottom > 2)
     return fail(VFE_EINVAL, "fix_bottom must be 0, 1 or 2");
+  if (opt.stencil != 0 && opt.stencil != 1) return fail(VFE_EINVAL, "stencil must be 0 or 1");
 
   vfe_mesh *m = new vfe_mesh();
   m->nx = nx; m->ny = ny; m->nz = nz; m->h = h; m->opt = opt; m->device = opt.device;
@@ -537,17 +575,154 @@ static std::vector<int64_t> tc_update_multipliers(const vfe_mesh *m) {
   return C;
 }
 
-// TMA map over a padded SoA int64 nodal array: (x, y, z, component), box 18x17x1x3
-static int encode_state_tmap(const vfe_mesh *m, EncodeTiledFn enc, void *base, CUtensorMap *map) {
+// TMA map over a padded SoA int64 nodal array: (x, y, z, component), box
+// 18x17x1x3 (element kernel) or 20x18x1x3 (node-stencil kernel)
+static int encode_state_tmap(const vfe_mesh *m, EncodeTiledFn enc, void *base, CUtensorMap *map,
+                             bool stencil_box = false) {
   cuuint64_t dims[4] = {(cuuint64_t)m->nxp, (cuuint64_t)m->nyp, (cuuint64_t)(m->nz + 1), 3};
   cuuint64_t strides[3] = {(cuuint64_t)m->nxp * 8, (cuuint64_t)m->plane * 8,
                            (cuuint64_t)m->comp * 8};
-  cuuint32_t box[4] = {TC_BOXX, TC_NODES, 1, 3};
+  cuuint32_t box[4] = {stencil_box ? (cuuint32_t)ST_BOXX : (cuuint32_t)TC_BOXX,
+                       stencil_box ? (cuuint32_t)ST_BOXY : (cuuint32_t)TC_NODES, 1, 3};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, base, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return VFE_OK;
+}
+
+// Runs (column x, column y, z0, z1) in order cut into at most `sms` ranges
+// of equal plane counts, one per CTA; every piece of a run is a segment.
+static void split_runs(const std::vector<int4> &runs, const std::vector<int32_t> *run_mat,
+                       int sms, std::vector<int4> &segs, std::vector<int32_t> *seg_mat,
+                       std::vector<int32_t> &off) {
+  int64_t total = 0;
+  for (const int4 &r : runs) total += r.w - r.z;
+  const int64_t G = total > 0 ? std::min<int64_t>(sms, total) : 0;
+  segs.clear();
+  if (seg_mat) seg_mat->clear();
+  off.assign(G + 1, 0);
+  size_t ri = 0;
+  int64_t used = 0;  // planes of runs[ri] already given out
+  for (int64_t b = 0; b < G; ++b) {
+    off[b] = (int32_t)segs.size();
+    int64_t want = (b + 1) * total / G - b * total / G;
+    while (want > 0) {
+      const int4 r = runs[ri];
+      const int64_t take = std::min<int64_t>(r.w - r.z - used, want);
+      segs.push_back(make_int4(r.x, r.y, (int)(r.z + used), (int)(r.z + used + take)));
+      if (seg_mat) seg_mat->push_back((*run_mat)[ri]);
+      used += take;
+      want -= take;
+      if (used == r.w - r.z) {
+        ++ri;
+        used = 0;
+      }
+    }
+  }
+  off[G] = (int32_t)segs.size();
+}
+
+template <typename T>
+static int upload_vec(T **dptr, const std::vector<T> &v) {
+  if (*dptr) cudaFree(*dptr);
+  *dptr = nullptr;
+  CUDA_TRY(cudaMalloc(dptr, sizeof(T) * std::max<size_t>(v.size(), 1)));
+  if (!v.empty())
+    CUDA_TRY(cudaMemcpy(*dptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return VFE_OK;
+}
+
+// Work decomposition of the TC path.  Column-plane (15x15 node column, one
+// node plane) classes: uniform material m when every element around the
+// column's nodes on both sides of the plane has material m and the column is
+// inside the mesh (node-stencil kernel); void when every such element is void
+// or outside the mesh (massless nodes stay at rest: no work); mixed otherwise,
+// and always for planes holding the source or a receiver (element kernel).
+// With the node-stencil kernel off (option, or Rayleigh damping) every
+// column-plane goes to the element kernel, as does the exact-partials list.
+static int build_segments(vfe_mesh *m) {
+  const int nx = m->nx, ny = m->ny, nz = m->nz, TX = m->tiles_x, TY = m->tiles_y;
+  const int planes = nz + 1;
+  m->stencil_on = m->opt.path == VFE_PATH_TC && m->opt.stencil != 0 && !m->damped;
+  std::vector<int4> all_runs, el_runs, st_runs;
+  std::vector<int32_t> st_rmat;
+  std::vector<char> forced((size_t)TX * TY * planes, 0);
+  auto force = [&](int64_t n) {
+    const int i = (int)(n % (nx + 1)), j = (int)((n / (nx + 1)) % (ny + 1));
+    const int k = (int)(n / ((int64_t)(nx + 1) * (ny + 1)));
+    forced[((size_t)(j / TC_OWN) * TX + i / TC_OWN) * planes + k] = 1;
+  };
+  if (m->has_src) force(m->src_node);
+  for (int r = 0; r < m->n_rec; ++r) force(m->rec_nodes[r]);
+  std::vector<int> layer(nz);
+  for (int ty = 0; ty < TY; ++ty)
+    for (int tx = 0; tx < TX; ++tx) {
+      all_runs.push_back(make_int4(tx, ty, 0, planes));
+      if (!m->stencil_on) continue;
+      // elements around the owned nodes: x in [15 tx - 1, 15 tx + 15), y likewise
+      const int ex0 = TC_OWN * tx - 1, ex1 = TC_OWN * tx + TC_OWN;
+      const int ey0 = TC_OWN * ty - 1, ey1 = TC_OWN * ty + TC_OWN;
+      const bool inside = ex0 >= 0 && ex1 <= nx && ey0 >= 0 && ey1 <= ny;
+      const int cx0 = std::max(ex0, 0), cx1 = std::min(ex1, nx);
+      const int cy0 = std::max(ey0, 0), cy1 = std::min(ey1, ny);
+      for (int ez = 0; ez < nz; ++ez) {  // per element layer: material, -1 void, -2 mixed
+        int v = m->mat[(size_t)cx0 + (size_t)nx * (cy0 + (size_t)ny * ez)];
+        for (int ey = cy0; ey < cy1 && v != -2; ++ey) {
+          const int32_t *row = &m->mat[(size_t)nx * (ey + (size_t)ny * ez)];
+          for (int ex = cx0; ex < cx1; ++ex)
+            if (row[ex] != v) { v = -2; break; }
+        }
+        if (!inside && v >= 0) v = -2;  // solid next to the outside
+        layer[ez] = v;
+      }
+      int run_cls = -3, run_z0 = 0;
+      auto flush = [&](int z1) {
+        if (run_cls == -2) el_runs.push_back(make_int4(tx, ty, run_z0, z1));
+        if (run_cls >= 0) {
+          st_runs.push_back(make_int4(tx, ty, run_z0, z1));
+          st_rmat.push_back(run_cls);
+        }
+      };
+      for (int L = 0; L < planes; ++L) {
+        const int a = L > 0 ? layer[L - 1] : -1, b = L < nz ? layer[L] : -1;
+        int cls = a == b ? a : -2;
+        if (forced[((size_t)ty * TX + tx) * planes + L]) cls = -2;
+        if (cls >= 0 && (L == 0 || L == nz)) cls = -2;
+        if (cls != run_cls) {
+          flush(L);
+          run_cls = cls;
+          run_z0 = L;
+        }
+      }
+      flush(planes);
+    }
+  std::vector<int32_t> all_off;
+  std::vector<int4> all_segs;
+  split_runs(all_runs, nullptr, m->sms, all_segs, nullptr, all_off);
+  m->all_ctas = (int)all_off.size() - 1;
+  int rc;
+  if ((rc = upload_vec(&m->d_all_segs, all_segs)) != VFE_OK) return rc;
+  if ((rc = upload_vec(&m->d_all_off, all_off)) != VFE_OK) return rc;
+  if (m->stencil_on) {
+    split_runs(el_runs, nullptr, m->sms, m->segs, nullptr, m->seg_off);
+    split_runs(st_runs, &st_rmat, m->sms, m->st_segs, &m->st_mat, m->st_off);
+  } else {
+    m->segs = all_segs;
+    m->seg_off = all_off;
+    m->st_segs.clear();
+    m->st_mat.clear();
+    m->st_off.assign(1, 0);
+  }
+  m->n_ctas = (int)m->seg_off.size() - 1;
+  m->st_ctas = (int)m->st_off.size() - 1;
+  if ((rc = upload_vec(&m->d_segs, m->segs)) != VFE_OK) return rc;
+  if ((rc = upload_vec(&m->d_seg_off, m->seg_off)) != VFE_OK) return rc;
+  if ((rc = upload_vec(&m->d_st_segs, m->st_segs)) != VFE_OK) return rc;
+  if ((rc = upload_vec(&m->d_st_mat, m->st_mat)) != VFE_OK) return rc;
+  if ((rc = upload_vec(&m->d_st_off, m->st_off)) != VFE_OK) return rc;
+  invalidate_graphs(m);
   return VFE_OK;
 }
 
@@ -615,38 +790,71 @@ static int build_tc(vfe_mesh *m) {
     if (!m->fixed[n]) cmax = std::max(cmax, m->dt * m->dt / m->mass[n]);
   m->eC = 61 - std::ilogb(cmax);
   // padded nodal layout (x pitch >= TMA box, y rows >= box)
-  m->nxp = ((std::max(nx + 1, TC_BOXX) + 3) / 4) * 4;
-  m->nyp = std::max(ny + 1, TC_NODES);
+  m->nxp = ((std::max(nx + 1, std::max(TC_BOXX, ST_BOXX)) + 3) / 4) * 4;
+  m->nyp = std::max(ny + 1, std::max(TC_NODES, ST_BOXY));
   m->plane = (int64_t)m->nxp * m->nyp;
   m->comp = m->plane * (nz + 1);
   std::vector<int64_t> C = tc_update_multipliers(m);
-  // work decomposition: the column-planes (15x15 node column, one node
-  // plane) in column order are split into one equal contiguous range per SM;
-  // each range becomes one or more segments (column, z0, z1)
   m->tiles_x = (nx + 1 + TC_OWN - 1) / TC_OWN;
   m->tiles_y = (ny + 1 + TC_OWN - 1) / TC_OWN;
+  // node-stencil B images (vfe_stencil.cu): per (variant v, dy) 16 K rows
+  // (x-shift d of the pair's first node - 1, component; rows 12..15 zero) x
+  // 80 N columns: five 16-column blocks, the contributions of an input plane
+  // p to the outputs p + o, o = -1, 0, 1, -1, 0 (column 8 node of the pair +
+  // 2 component + part; 6, 7, 14, 15 zero), K-major core matrices (N groups
+  // at 128 B, K groups at 1280 B).  Variant 1 zeroes the o = -1 blocks, variant 2 the
+  // o = -1 and o = 0 blocks.  Parts: S^k of K^kappa and S^G of
+  // Kbar^G = K^G' - 128 I, each summed over the eight elements around a node.
+  std::vector<uint16_t> bst(9 * 1280, 0);
   {
-    const int64_t planes = nz + 1, ncols = (int64_t)m->tiles_x * m->tiles_y;
-    const int64_t total = ncols * planes;
-    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(m->sms, total));
-    m->n_ctas = (int)G;
-    m->segs.clear();
-    m->seg_off.assign(G + 1, 0);
-    for (int64_t b = 0; b < G; ++b) {
-      m->seg_off[b] = (int32_t)m->segs.size();
-      int64_t lo = b * total / G;
-      const int64_t hi = (b + 1) * total / G;
-      while (lo < hi) {
-        const int64_t col = lo / planes, z0 = lo % planes;
-        const int64_t z1 = std::min<int64_t>(planes, z0 + (hi - lo));
-        m->segs.push_back(make_int4((int)(col % m->tiles_x), (int)(col / m->tiles_x), (int)z0,
-                                    (int)z1));
-        lo += z1 - z0;
+    int64_t Sk[27][9] = {}, Sg[27][9] = {};
+    for (int e = 0; e < 8; ++e) {
+      const int o[3] = {-(e & 1), -((e >> 1) & 1), -((e >> 2) & 1)};
+      const int a = -o[0] - 2 * o[1] - 4 * o[2];  // the node's corner in element e
+      for (int b = 0; b < 8; ++b) {
+        const int off = (o[0] + (b & 1) + 1) + 3 * (o[1] + ((b >> 1) & 1) + 1) +
+                        9 * (o[2] + ((b >> 2) & 1) + 1);
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            Sk[off][3 * i + j] += Ik[(3 * a + i) * 24 + 3 * b + j];
+            Sg[off][3 * i + j] += Ig[(3 * a + i) * 24 + 3 * b + j] - (a == b && i == j ? 128 : 0);
+          }
       }
     }
-    m->seg_off[G] = (int32_t)m->segs.size();
+    int64_t l1k = 0, l1g = 0;
+    for (int i = 0; i < 3; ++i) {
+      int64_t rk = 0, rg = 0;
+      for (int off = 0; off < 27; ++off)
+        for (int j = 0; j < 3; ++j) {
+          rk += std::llabs(Sk[off][3 * i + j]);
+          rg += std::llabs(Sg[off][3 * i + j]);
+          if (std::llabs(Sk[off][3 * i + j]) > 2048 || std::llabs(Sg[off][3 * i + j]) > 2048)
+            return fail(VFE_EINVAL, "internal: stencil entry not exact in fp16");
+        }
+      l1k = std::max(l1k, rk);
+      l1g = std::max(l1g, rg);
+    }
+    // fp32-exact partial sums inside the magic-bias window: row L1 x 1024 < 2^22
+    if (std::max(l1k, l1g) * 1024 >= (1 << 22))
+      return fail(VFE_EINVAL, "internal: stencil row norm too large");
+    for (int v = 0; v < 3; ++v)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int nn = 0; nn < 80; ++nn)
+          for (int k = 0; k < 12; ++k) {
+            const int blk = nn / 16, n = nn % 16;
+            const int o = blk % 3 - 1;  // output plane p + o
+            if ((v >= 1 && o == -1) || (v == 2 && o == 0) || n % 8 >= 6) continue;
+            const int j = n / 8, co = (n % 8) / 2, part = n % 2;  // column 8 j + 2 co + part
+            const int d = k / 3, c = k % 3, ox = (d - 1) - j;
+            if (ox < -1 || ox > 1) continue;
+            // input node = output node + (ox, dy, -o)
+            const int off = (ox + 1) + 3 * (dy + 1) + 9 * (-o + 1);
+            const float val = (float)(part == 0 ? Sk[off][3 * co + c] : Sg[off][3 * co + c]);
+            const int byte = (v * 3 + dy + 1) * 2560 + (nn / 8) * 128 + (k / 8) * 1280 +
+                             (nn % 8) * 16 + (k % 8) * 2;
+            bst[byte / 2] = __half_as_ushort(__float2half(val));
+          }
   }
-
   const size_t ubytes = sizeof(int64_t) * 3 * m->comp;
   CUDA_TRY(cudaMalloc(&m->d_U[0], ubytes));
   CUDA_TRY(cudaMalloc(&m->d_U[1], ubytes));
@@ -657,11 +865,8 @@ static int build_tc(vfe_mesh *m) {
   CUDA_TRY(cudaMalloc(&m->d_or, sizeof(unsigned long long) * or_words));
   CUDA_TRY(cudaMalloc(&m->d_tcparams, sizeof(TcStepParams)));
   CUDA_TRY(cudaMalloc(&m->d_tcpersist, sizeof(int64_t) * 8));
-  CUDA_TRY(cudaMalloc(&m->d_segs, sizeof(int4) * m->segs.size()));
-  CUDA_TRY(cudaMalloc(&m->d_seg_off, sizeof(int32_t) * m->seg_off.size()));
-  CUDA_TRY(cudaMemcpy(m->d_segs, m->segs.data(), sizeof(int4) * m->segs.size(),
-                      cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(m->d_seg_off, m->seg_off.data(), sizeof(int32_t) * m->seg_off.size(),
+  CUDA_TRY(cudaMalloc(&m->d_Bst, sizeof(uint16_t) * bst.size()));
+  CUDA_TRY(cudaMemcpy(m->d_Bst, bst.data(), sizeof(uint16_t) * bst.size(),
                       cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemset(m->d_U[0], 0, ubytes));
   CUDA_TRY(cudaMemset(m->d_U[1], 0, ubytes));
@@ -677,18 +882,18 @@ static int build_tc(vfe_mesh *m) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(VFE_ECUDA, "cuTensorMapEncodeTiled is not available");
   for (int b = 0; b < 2; ++b) {
-    const int rc = encode_state_tmap(m, enc, m->d_U[b], &m->tmap[b]);
+    int rc = encode_state_tmap(m, enc, m->d_U[b], &m->tmap[b]);
+    if (rc == VFE_OK) rc = encode_state_tmap(m, enc, m->d_U[b], &m->st_tmap[b], true);
     if (rc != VFE_OK) return rc;
   }
-  return VFE_OK;
+  CUDA_TRY(stencil_prepare());
+  return build_segments(m);
 }
 
-static int rebuild_receivers(vfe_mesh *m) {
-  // trace rows restart
-  m->trace_rows = 0;
+// the receivers of each element-kernel segment (the TC path) or the receiver
+// node list (FP64 path); the recorded trace rows are kept
+static int receiver_tables(vfe_mesh *m) {
   if (m->opt.path == VFE_PATH_TC) {
-    int64_t persist2 = 0;
-    CUDA_TRY(cudaMemcpy(m->d_tcpersist + 2, &persist2, sizeof(int64_t), cudaMemcpyHostToDevice));
     const int items = (int)m->segs.size();
     std::vector<std::vector<TcRecv>> per(items);
     for (int r = 0; r < m->n_rec; ++r) {
@@ -730,8 +935,6 @@ static int rebuild_receivers(vfe_mesh *m) {
     CUDA_TRY(cudaMemcpy(m->d_recv_off, off.data(), sizeof(int32_t) * off.size(),
                         cudaMemcpyHostToDevice));
   } else {
-    int64_t z = 0;
-    CUDA_TRY(cudaMemcpy(m->d_f64persist + 1, &z, sizeof(int64_t), cudaMemcpyHostToDevice));
     if (m->d_recnodes) cudaFree(m->d_recnodes);
     m->d_recnodes = nullptr;
     CUDA_TRY(cudaMalloc(&m->d_recnodes, sizeof(int64_t) * std::max(m->n_rec, 1)));
@@ -741,6 +944,29 @@ static int rebuild_receivers(vfe_mesh *m) {
   }
   invalidate_graphs(m);
   return VFE_OK;
+}
+
+// segments (TC path: they depend on the source and receiver nodes, and on
+// damping) and receiver tables after a change of either
+static int rebuild_work(vfe_mesh *m) {
+  if (m->opt.path == VFE_PATH_TC) {
+    const int rc = build_segments(m);
+    if (rc != VFE_OK) return rc;
+  }
+  return receiver_tables(m);
+}
+
+// new receivers: the trace rows restart
+static int rebuild_receivers(vfe_mesh *m) {
+  m->trace_rows = 0;
+  if (m->opt.path == VFE_PATH_TC) {
+    int64_t persist2 = 0;
+    CUDA_TRY(cudaMemcpy(m->d_tcpersist + 2, &persist2, sizeof(int64_t), cudaMemcpyHostToDevice));
+  } else {
+    int64_t z = 0;
+    CUDA_TRY(cudaMemcpy(m->d_f64persist + 1, &z, sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
+  return rebuild_work(m);
 }
 
 extern "C" {
@@ -767,7 +993,7 @@ int vfe_set_source(vfe_mesh *m, int i, int j, int k, const double dir[3], double
   m->amp = amp;
   m->src_scale = m->has_src ? m->dt * m->dt / m->mass[n] : 0.0;
   invalidate_graphs(m);
-  return VFE_OK;
+  return rebuild_work(m);
 }
 
 int vfe_set_receivers(vfe_mesh *m, int n, const int32_t *ijk) {
@@ -1109,6 +1335,7 @@ int vfe_set_damping(vfe_mesh *m, double alpha, double beta) {
   if (m->opt.path == VFE_PATH_TC) {  // the update multipliers carry 1 / (1 + alpha dt / 2)
     const std::vector<int64_t> C = tc_update_multipliers(m);
     CUDA_TRY(cudaMemcpy(m->d_C, C.data(), sizeof(int64_t) * C.size(), cudaMemcpyHostToDevice));
+    if ((rc = rebuild_work(m)) != VFE_OK) return rc;  // damped steps: element kernel only
   }
   invalidate_graphs(m);
   return vfe_set_state(m, u.data(), up.data());
@@ -1175,25 +1402,36 @@ static int tc_apply(vfe_mesh *m, const double *u, int mode, std::vector<int64_t>
       rc = fail(VFE_ECUDA, "upload: %s", cudaGetErrorString(e));
       break;
     }
-    // a tensor map over the scratch copy of u
-    CUtensorMap tm;
-    cuuint64_t dims[4] = {(cuuint64_t)m->nxp, (cuuint64_t)m->nyp, (cuuint64_t)(m->nz + 1), 3};
-    cuuint64_t strides[3] = {(cuuint64_t)m->nxp * 8, (cuuint64_t)m->plane * 8,
-                             (cuuint64_t)m->comp * 8};
-    cuuint32_t box[4] = {TC_BOXX, TC_NODES, 1, 3};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    CUresult r = encode_fn()(&tm, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, dU, dims, strides, box, es,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) { rc = fail(VFE_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r); break; }
+    // tensor maps over the scratch copy of u (element and node-stencil boxes)
+    CUtensorMap tm, tms;
+    if ((rc = encode_state_tmap(m, encode_fn(), dU, &tm)) != VFE_OK ||
+        (rc = encode_state_tmap(m, encode_fn(), dU, &tms, true)) != VFE_OK)
+      break;
     TcDevice d = tc_device(m, m->cur);
     d.params = dp;
     d.src_node = -1;
     d.n_rec = 0;
     d.S_out = mode == TC_MODE_KU ? dout : nullptr;
     d.partials_out = mode == TC_MODE_PARTIALS ? dout : nullptr;
-    if ((e = tc_launch_step(m->stream, d, &tm, mode)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
+    if (mode == TC_MODE_PARTIALS) {  // every element, on the element kernel
+      d.segs = m->d_all_segs;
+      d.seg_off = m->d_all_off;
+      d.n_ctas = m->all_ctas;
+    }
+    if (d.n_ctas > 0 && (e = tc_launch_step(m->stream, d, &tm, mode)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "K u kernel: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (mode == TC_MODE_KU && m->stencil_on) {  // the uniform runs
+      TcDevice ds = tc_stencil_device(m, m->cur);
+      ds.params = dp;
+      ds.S_out = dout;
+      if ((e = stencil_launch(m->stream, ds, &tms, TC_MODE_KU)) != cudaSuccess) {
+        rc = fail(VFE_ECUDA, "node-stencil K u kernel: %s", cudaGetErrorString(e));
+        break;
+      }
+    }
+    if ((e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
       rc = fail(VFE_ECUDA, "K u kernel: %s", cudaGetErrorString(e));
       break;
     }
@@ -1273,15 +1511,19 @@ int vfe_mesh_view(vfe_mesh *m, VfeMeshView *v) {
   v->tc = m->opt.path == VFE_PATH_TC ? 1 : 0;
   v->stream = m->stream;
   v->dev = tc_device(m, m->cur);
+  v->stencil_on = m->stencil_on ? 1 : 0;
+  v->st = tc_stencil_device(m, m->cur);
   return VFE_OK;
 }
 
-CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v) {
+CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v,
+                              bool stencil_box) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return CUDA_ERROR_NOT_SUPPORTED;
   cuuint64_t dims[4] = {(cuuint64_t)v.nxp, (cuuint64_t)v.nyp, (cuuint64_t)(v.nz + 1), 3};
   cuuint64_t strides[3] = {(cuuint64_t)v.nxp * 8, (cuuint64_t)v.plane * 8, (cuuint64_t)v.comp * 8};
-  cuuint32_t box[4] = {TC_BOXX, TC_NODES, 1, 3};
+  cuuint32_t box[4] = {stencil_box ? (cuuint32_t)ST_BOXX : (cuuint32_t)TC_BOXX,
+                       stencil_box ? (cuuint32_t)ST_BOXY : (cuuint32_t)TC_NODES, 1, 3};
   cuuint32_t es[4] = {1, 1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, base, dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1289,6 +1531,78 @@ CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v
 }
 
 extern "C" {
+
+int vfe_debug_stencil_partials(vfe_mesh *m, const double *u, int64_t *out, int8_t *covered,
+                               int *shift_out, int *frac_bits_out) {
+  if (!m || !u || !out || !covered) return fail(VFE_EINVAL, "NULL argument");
+  if (m->opt.path != VFE_PATH_TC) return fail(VFE_ESTATE, "mesh is not on the tensor-core path");
+  for (int64_t i = 0; i < 3 * m->nn; ++i)
+    if (!std::isfinite(u[i])) return fail(VFE_EINVAL, "u has non-finite values");
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  const int F = pick_frac_bits(u, nullptr, 3 * m->nn);
+  std::vector<int64_t> U;
+  unsigned long long orv = 0;
+  to_fixed(m, u, F, U, false, &orv);
+  const int shq = std::max(0, bitlen(orv) - TC_QBITS);
+  std::vector<char> cov(m->nn, 0);
+  if (m->stencil_on)
+    for (const int4 &q : m->st_segs)
+      for (int k = q.z; k < q.w; ++k)
+        for (int j = TC_OWN * q.y; j < std::min(TC_OWN * q.y + TC_OWN, m->ny + 1); ++j)
+          for (int i = TC_OWN * q.x; i < std::min(TC_OWN * q.x + TC_OWN, m->nx + 1); ++i)
+            cov[node_id(m, i, j, k)] = 1;
+  int64_t *dU = nullptr, *dout = nullptr;
+  TcStepParams *dp = nullptr;
+  const size_t ubytes = sizeof(int64_t) * U.size(), obytes = 3 * ubytes;
+  int rc = VFE_OK;
+  cudaError_t e;
+  do {
+    if ((e = cudaMalloc(&dU, ubytes)) != cudaSuccess || (e = cudaMalloc(&dout, obytes)) != cudaSuccess ||
+        (e = cudaMalloc(&dp, sizeof(TcStepParams))) != cudaSuccess) {
+      rc = fail(VFE_ENOMEM, "scratch allocation: %s", cudaGetErrorString(e));
+      break;
+    }
+    TcStepParams p;
+    memset(&p, 0, sizeof(p));
+    p.trace_row = -1;
+    p.shq = shq;
+    p.F = F;
+    if ((e = cudaMemcpy(dU, U.data(), ubytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(dout, 0, obytes)) != cudaSuccess ||
+        (e = cudaMemcpy(dp, &p, sizeof(p), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "upload: %s", cudaGetErrorString(e));
+      break;
+    }
+    CUtensorMap tms;
+    if ((rc = encode_state_tmap(m, encode_fn(), dU, &tms, true)) != VFE_OK) break;
+    TcDevice ds = tc_stencil_device(m, m->cur);
+    ds.params = dp;
+    ds.partials_out = dout;
+    if ((e = stencil_launch(m->stream, ds, &tms, TC_MODE_PARTIALS)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(m->stream)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "node-stencil partials: %s", cudaGetErrorString(e));
+      break;
+    }
+    if ((rc = check_status(m)) != VFE_OK) break;
+    std::vector<int64_t> P(obytes / sizeof(int64_t));
+    if ((e = cudaMemcpy(P.data(), dout, obytes, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+      rc = fail(VFE_ECUDA, "download: %s", cudaGetErrorString(e));
+      break;
+    }
+    for (int64_t n = 0; n < m->nn; ++n) {
+      const int64_t t = tc_index(m, n);
+      covered[n] = cov[n];
+      for (int c = 0; c < 9; ++c) out[9 * n + c] = cov[n] ? P[c * m->comp + t] : 0;
+    }
+  } while (0);
+  if (dU) cudaFree(dU);
+  if (dout) cudaFree(dout);
+  if (dp) cudaFree(dp);
+  if (shift_out) *shift_out = shq;
+  if (frac_bits_out) *frac_bits_out = F;
+  return rc;
+}
 
 int vfe_debug_inject_status(vfe_mesh *m, int bits) {
   if (!m) return fail(VFE_EINVAL, "NULL mesh");

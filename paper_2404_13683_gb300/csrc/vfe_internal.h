@@ -24,6 +24,8 @@
 #define TC_THREADS 512          // two threads per element: corner groups dz = 0 / 1
 #define TC_MAX_MAT 64            // materials per mesh on the TC path
 #define TC_MAX_REC_CTA 64        // receivers handled per CTA work item
+#define ST_BOXX 20               // stencil kernel: TMA box width in x (int64; 160 B)
+#define ST_BOXY 18               // stencil kernel: node rows per box
 #define TC_UNITS_BITS 59         // target bit length of max |U| after rescale
                                  // (a step's growth keeps |U| below 2^62)
 
@@ -100,6 +102,10 @@ struct TcDevice {         // everything the TC kernels read (by value)
   int64_t *W_next;
   int64_t dG, dH, dB;
   int damped;
+  // node-stencil kernel (vfe_stencil.cu): its own segments, their material
+  // and its B operand image (9 neighbour rows x 16 x 16 fp16)
+  const int32_t *seg_mat;
+  const uint16_t *Bst;
 };
 
 // Several meshes advanced by one launch: each segment belongs to one mesh,
@@ -183,11 +189,14 @@ struct VfeMeshView {
   int tc;                 // 1 on the tensor-core path
   cudaStream_t stream;
   TcDevice dev;           // kernel arguments with the mesh's own pointers
+  int stencil_on;         // the node-stencil kernel takes the uniform runs
+  TcDevice st;            // its arguments (segments, materials, B image)
 };
 int vfe_mesh_view(vfe_mesh *mesh, VfeMeshView *view);
 void vfe_set_last_error(const char *msg);  // message returned by vfe_last_error()
 // tensor map of a padded SoA int64 nodal array laid out like the state
-CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v);
+CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v,
+                              bool stencil_box = false);
 
 // launch helpers implemented in the .cu files ---------------------------------
 enum { TC_MODE_STEP = 0, TC_MODE_KU = 1, TC_MODE_PARTIALS = 2 };
@@ -201,6 +210,10 @@ cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t 
 cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
 cudaError_t tc_launch_batch_prologue(cudaStream_t s, const TcPrologueArgs *args, int n_meshes);
 cudaError_t tc_launch_batch_step(cudaStream_t s, const TcBatch &b, int stages);
+cudaError_t stencil_prepare();
+// the node-stencil kernel over d.segs / d.seg_off / d.seg_mat (d.n_ctas CTAs;
+// nothing is launched for 0); tmap: box ST_BOXX x ST_BOXY x 1 x 3
+cudaError_t stencil_launch(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
 
 cudaError_t tc_state_to_f64(cudaStream_t s, const int64_t *U, const int64_t *persist,
                             int extra_shift, int nx, int ny, int64_t nn, int nxp, int64_t plane,

@@ -190,17 +190,26 @@ int vfe_internal_force_noalloc(vfe_mesh *mesh, const double *u, double *f) {
                                                      v.ny, v.nn, v.nxp, v.plane, v.comp, maxbits,
                                                      regA, params);
   NA_TRY(cudaGetLastError());
-  // K u of the fixed-point copy (region A) into region B
-  CUtensorMap map;
-  if (vfe_encode_state_map(&map, regA, v) != CUDA_SUCCESS)
+  // K u of the fixed-point copy (region A) into region B, cleared first: the
+  // kernels write every node that has a solid element, the rest stay zero
+  CUtensorMap map, smap;
+  if (vfe_encode_state_map(&map, regA, v) != CUDA_SUCCESS ||
+      vfe_encode_state_map(&smap, regA, v, true) != CUDA_SUCCESS)
     return set_err(VFE_ECUDA, "cuTensorMapEncodeTiled failed for the no-alloc scratch");
+  NA_TRY(cudaMemsetAsync(regB, 0, region, s));
   TcDevice d = v.dev;
   d.params = params;
   d.src_node = -1;
   d.n_rec = 0;
   d.S_out = regB;
   d.partials_out = nullptr;
-  NA_TRY(tc_launch_step(s, d, &map, TC_MODE_KU));
+  if (d.n_ctas > 0) NA_TRY(tc_launch_step(s, d, &map, TC_MODE_KU));
+  if (v.stencil_on) {
+    TcDevice ds = v.st;
+    ds.params = params;
+    ds.S_out = regB;
+    NA_TRY(stencil_launch(s, ds, &smap, TC_MODE_KU));
+  }
   // S -> f (FP64 AoS) in region A, then to the caller
   noalloc_from_fixed_kernel<<<blocks, threads, 0, s>>>(regB, v.nx, v.ny, v.nn, v.nxp, v.plane,
                                                        v.comp, v.e_ref, params,

@@ -35,7 +35,7 @@ EXPORTS = (
     "vfe_get_trace_rows", "vfe_internal_force_noalloc",
     "vfe_create_batch", "vfe_batch_step", "vfe_batch_synchronize", "vfe_destroy_batch",
     "vfe_misfit_gradient", "vfe_step_forced", "vfe_set_damping", "vfe_rayleigh_coefficients",
-    "vfe_get_trace_rows_async", "vfe_debug_inject_status",
+    "vfe_get_trace_rows_async", "vfe_debug_inject_status", "vfe_debug_stencil_partials",
 )
 
 
@@ -49,7 +49,7 @@ class vfe_options(ctypes.Structure):
     _fields_ = [("element_kind", ctypes.c_int), ("path", ctypes.c_int), ("stages", ctypes.c_int),
                 ("fix_bottom", ctypes.c_int), ("dt", ctypes.c_double),
                 ("cfl_fraction", ctypes.c_double), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("stencil", ctypes.c_int)]
 
 
 _lib = None
@@ -101,6 +101,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_last_error.restype = ctypes.c_char_p
     L.vfe_debug_tc_partials.argtypes = [P, P, I, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
     L.vfe_debug_inject_status.argtypes = [P, I]
+    L.vfe_debug_stencil_partials.argtypes = [P, P, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
     for name in EXPORTS:
         if name not in ("vfe_default_options", "vfe_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -292,6 +293,19 @@ def vfe_misfit_gradient(mesh, data, checkpoint_every=100):
     return grad, J.value
 
 
+def vfe_debug_stencil_partials(mesh, u):
+    """(out [nodes][9] int64: P, S^G q, q'; covered [nodes] bool; shift; frac
+    bits) of the node-stencil kernel for u."""
+    nn, _ = vfe_get_sizes(mesh)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+    out = np.zeros((nn, 9), dtype=np.int64)
+    cov = np.zeros(nn, dtype=np.int8)
+    sh, F = ctypes.c_int(), ctypes.c_int()
+    _check(load().vfe_debug_stencil_partials(mesh, _p(u), _p(out), _p(cov), ctypes.byref(sh),
+                                             ctypes.byref(F)))
+    return out, cov.astype(bool), sh.value, F.value
+
+
 def vfe_create_batch(handles):
     arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
                                              for h in handles])
@@ -349,7 +363,8 @@ class Mesh:
     (see ``workloads.py``)."""
 
     def __init__(self, workload, path=VFE_PATH_TC, kind=VFE_OVFEM, stages=5, dt=None,
-                 fix_bottom=None, stream=None, device=0, source=True, receivers=True):
+                 fix_bottom=None, stream=None, device=0, source=True, receivers=True,
+                 stencil=True):
         nx, ny, nz = workload["shape"]
         if dt is None:
             dt = float(workload.get("dt", 0.0))
@@ -357,7 +372,7 @@ class Mesh:
             fix_bottom = workload.get("fix_bottom", 1)
         opt = vfe_default_options(element_kind=kind, path=path, stages=stages, dt=dt,
                                   fix_bottom=int(fix_bottom), device=device,
-                                  stream=stream or 0)
+                                  stream=stream or 0, stencil=1 if stencil else 0)
         self.handle = vfe_create_mesh(nx, ny, nz, workload["h"], workload["material_ids"],
                                       workload["material_table"], opt)
         self.workload = workload
