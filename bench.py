@@ -60,6 +60,10 @@ def parse():
                     help="config3 (default: 512x512x256, the largest single-GPU model) is the "
                          "headline; config2 (128x128x64) and the others are reported in the "
                          "design notes")
+    ap.add_argument("--decomp", choices=["replicas", "slab"], default="replicas",
+                    help="with --gpus N > 1: independent replicas (default, weak scaling) or "
+                         "one model split into N z-slabs with a node-plane exchange per step "
+                         "(strong scaling)")
     ap.add_argument("--shape", default=None,
                     help="NX,NY,NZ: the config3 generator at another size (for profiling a "
                          "smaller model of the same kind; the headline is 512,512,256)")
@@ -313,6 +317,8 @@ def run_ours(args):
 
     if args.workload == "config4":
         return run_batch(args, torch, dist, world, rank, local, vfe, W)
+    if args.decomp == "slab":
+        return run_slabs(args, torch, dist, world, rank, local, vfe, W)
     if args.workload == "config5":
         return run_adjoint(args, torch, dist, world, rank, local, vfe, W)
     mesh = make_workload(args, W)
@@ -476,6 +482,65 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_slabs(args, torch, dist, world, rank, local, vfe, W):
+    """One model split into `world` z-slabs (slab.py): every step, each rank
+    steps its slab, exchanges its boundary node planes with its neighbours
+    (NCCL send/recv on the mesh's stream) and all ranks agree on the
+    fixed-point unit (one 8-byte all-reduce).  value = the model's
+    element*steps per second (strong scaling)."""
+    from paper_2404_13683_gb300 import slab as S
+    mesh = make_workload(args, W)
+    ne = int(mesh["material_ids"].size)
+    # the model's time step: the minimum over the slabs' critical steps
+    probe = S.Slab(mesh, world, rank, 0.0)
+    w = dict(probe.workload)
+    w.pop("dt")
+    with vfe.Mesh(w, path=vfe.VFE_PATH_TC, stages=args.stages, device=local) as m:
+        dt_local = m.dt
+    t = torch.tensor([dt_local], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    slab = S.Slab(mesh, world, rank, float(t.item()))
+    eng = S.GpuSlabEngine(slab, torch, stages=args.stages)
+    eng.set_source_bound(S.source_scale(slab, eng, dist))
+    bufs = [torch.zeros(slab.plane_values(), dtype=torch.float64, device="cuda")
+            for _ in range(4)]
+
+    def one_step():
+        eng.step()
+        if dist is not None:
+            S.exchange(slab, eng, dist, bufs)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    eng.mesh.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(eng.stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(eng.stream)
+    torch.cuda.synchronize()
+    eng.mesh.synchronize()
+    ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+    eng.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": ne * args.steps / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "%s split into %d z-slabs (node-plane exchange per step)"
+                                   % (mesh["name"], world), "elements": ne,
+                       "slab_planes": S.plane_ranges(mesh["shape"][2], world),
+                       "timing": "CUDA events on rank 0's mesh stream, max over ranks; L2 not "
+                                 "flushed (the exchange separates the steps)"},
+            "parallelism": "slab x%d" % world}), flush=True)
 
 
 def run_batch(args, torch, dist, world, rank, local, vfe, W):

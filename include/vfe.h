@@ -205,6 +205,45 @@ int vfe_debug_tc_partials(vfe_mesh *mesh, const double *u, int n,
                           const int64_t *ids, int64_t *out, int *shift_out,
                           int *frac_bits_out);
 
+/* Node-plane exchange for a z-slab decomposition over several GPUs (the
+ * paper's closing remark that the method extends to multiple GPUs, Section
+ * 4).  A mesh that is one slab of a larger model holds, besides its own node
+ * planes, the plane just below and just above them; after every step the
+ * caller copies its own boundary planes of u^n to the neighbouring slabs and
+ * writes the planes it receives into its halo planes, so that the next step
+ * forms K u (Eq. DGE:ORG) on its own planes from the full neighbourhood.
+ * Both calls are queued on the mesh's stream (no wait) and move FP64 values:
+ * vfe_pack_plane writes u^n of node plane k (0 <= k <= nz, local to the mesh)
+ * to dev_out, a device array [(ny+1)(nx+1)][3] of vfe_plane_values doubles;
+ * vfe_unpack_plane writes such an array into u^n of plane k.  On the
+ * tensor-core path the value is rounded to the mesh's fixed-point unit (the
+ * same rounding the update applies) and enters the bounds from which the
+ * next step picks its digit quantum.  u^{n-1} is not touched.  VFE_ESTATE
+ * with Rayleigh damping (its state w would need the exchange too). */
+int vfe_plane_values(vfe_mesh *mesh, int64_t *n_values);
+int vfe_pack_plane(vfe_mesh *mesh, int k, double *dev_out);
+int vfe_unpack_plane(vfe_mesh *mesh, int k, const double *dev_in);
+
+/* One fixed-point scale for all slabs (tensor-core path).  Each step picks
+ * the power-of-two unit of the state from a bound of |u| and of the source
+ * increment (the digit quantum of Eq. intscaling and the update's unit);
+ * slabs that exchange planes must pick the same unit every step.  So after
+ * the exchange the caller takes the maximum of the slabs' bound words (an
+ * all-reduce MAX of one uint64 per slab): vfe_get_scale_bound copies the
+ * word the next step reads into dev_word (device, 8 bytes), and
+ * vfe_set_scale_bound writes the reduced word back (both queued on the
+ * mesh's stream; no-ops on the FP64 path, which has no scale).  A slab
+ * without the source learns the source from vfe_set_source_bound (the
+ * wavelet of vfe_set_source and dt^2/m at the source node, which the slab
+ * holding it reports through vfe_get_source_scale): it then sizes the unit
+ * for the source's increment as the source's slab does, without applying
+ * any force.  VFE_ESTATE if the mesh holds a source itself. */
+int vfe_get_scale_bound(vfe_mesh *mesh, unsigned long long *dev_word);
+int vfe_set_scale_bound(vfe_mesh *mesh, const unsigned long long *dev_word);
+int vfe_get_source_scale(vfe_mesh *mesh, double *dt2_over_m);
+int vfe_set_source_bound(vfe_mesh *mesh, const double dir[3], double f0_hz, double t0_s,
+                         double amp, double dt2_over_m);
+
 /* Exact integer partial sums of the node-stencil kernel: for u (FP64
  * [nodes][3], host) digitised as the kernel does (q = floor(U / 2^shift) of
  * the fixed-point state U = round(u 2^frac_bits)), out[node][9] int64 holds

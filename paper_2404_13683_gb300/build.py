@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libvfe.so")
 SOURCES = ["vfe_api.cu", "vfe_tc.cu", "vfe_stencil.cu", "vfe_fp64.cu", "vfe_noalloc.cu",
-           "vfe_adjoint.cu"]
+           "vfe_adjoint.cu", "vfe_slab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -148,6 +148,8 @@ struct vfe_mesh {
   std::vector<int32_t> rec_ijk;
 
   bool has_src = false;
+  bool src_bound_only = false;  // the source lies in another slab: it only
+                                // enters the choice of the fixed-point scale
   bool src_set = false;  // vfe_set_source was called
   int64_t src_node = -1;
   double src_dir[3] = {0, 0, 0}, f0 = 0, t0 = 0, amp = 0;
@@ -302,7 +304,8 @@ static int enqueue_step(vfe_mesh *m, int cur) {
     src.amp_scale = m->amp * m->src_scale * g;
     src.force_scale = m->src_scale * g;
     CUDA_TRY(tc_launch_prologue_ex(m->stream, m->d_tcparams, m->d_tcpersist, src, m->d_or,
-                                   m->tiles_x * m->tiles_y, m->has_src ? 1 : 0, trace_on,
+                                   m->tiles_x * m->tiles_y,
+                                   (m->has_src || m->src_bound_only) ? 1 : 0, trace_on,
                                    m->d_status, m->d_inj, 3 * m->n_rec));
     TcDevice d = tc_device(m, cur);
     if (d.n_ctas > 0)
@@ -592,36 +595,46 @@ static int encode_state_tmap(const vfe_mesh *m, EncodeTiledFn enc, void *base, C
   return VFE_OK;
 }
 
-// Runs (column x, column y, z0, z1) in order cut into at most `sms` ranges
-// of equal plane counts, one per CTA; every piece of a run is a segment.
+// Runs (column x, column y, z0, z1) in order cut into at most `sms` CTA
+// ranges of equal cost, a segment costing its planes plus `seg_cost` (the
+// fixed work of starting one: its first planes' copies and digits); a run is
+// cut where a range is full, and every piece is a segment.
 static void split_runs(const std::vector<int4> &runs, const std::vector<int32_t> *run_mat,
-                       int sms, std::vector<int4> &segs, std::vector<int32_t> *seg_mat,
-                       std::vector<int32_t> &off) {
-  int64_t total = 0;
-  for (const int4 &r : runs) total += r.w - r.z;
-  const int64_t G = total > 0 ? std::min<int64_t>(sms, total) : 0;
+                       int sms, double seg_cost, std::vector<int4> &segs,
+                       std::vector<int32_t> *seg_mat, std::vector<int32_t> &off) {
+  double total = 0.0;
+  int64_t planes = 0;
+  for (const int4 &r : runs) {
+    total += (r.w - r.z) + seg_cost;
+    planes += r.w - r.z;
+  }
+  const int64_t G = planes > 0 ? std::min<int64_t>(sms, planes) : 0;
   segs.clear();
   if (seg_mat) seg_mat->clear();
   off.assign(G + 1, 0);
-  size_t ri = 0;
-  int64_t used = 0;  // planes of runs[ri] already given out
-  for (int64_t b = 0; b < G; ++b) {
-    off[b] = (int32_t)segs.size();
-    int64_t want = (b + 1) * total / G - b * total / G;
-    while (want > 0) {
-      const int4 r = runs[ri];
-      const int64_t take = std::min<int64_t>(r.w - r.z - used, want);
-      segs.push_back(make_int4(r.x, r.y, (int)(r.z + used), (int)(r.z + used + take)));
-      if (seg_mat) seg_mat->push_back((*run_mat)[ri]);
-      used += take;
-      want -= take;
-      if (used == r.w - r.z) {
-        ++ri;
-        used = 0;
+  int64_t b = 0;      // CTA being filled
+  double have = 0.0;  // cost given to CTAs 0..b
+  for (size_t ri = 0; ri < runs.size(); ++ri) {
+    const int4 r = runs[ri];
+    int64_t z = r.z;
+    while (z < r.w) {
+      int64_t take = r.w - z;
+      if (b + 1 < G) {
+        const double room = total * (double)(b + 1) / (double)G - have - seg_cost;
+        if (room < 1.0 && (int64_t)segs.size() > off[b]) {  // CTA b is full
+          ++b;
+          off[b] = (int32_t)segs.size();
+          continue;
+        }
+        take = std::max<int64_t>(1, std::min<int64_t>(take, (int64_t)std::llround(room)));
       }
+      segs.push_back(make_int4(r.x, r.y, (int)z, (int)(z + take)));
+      if (seg_mat) seg_mat->push_back((*run_mat)[ri]);
+      have += (double)take + seg_cost;
+      z += take;
     }
   }
-  off[G] = (int32_t)segs.size();
+  for (int64_t k = b + 1; k <= G; ++k) off[k] = (int32_t)segs.size();
 }
 
 template <typename T>
@@ -700,14 +713,14 @@ static int build_segments(vfe_mesh *m) {
     }
   std::vector<int32_t> all_off;
   std::vector<int4> all_segs;
-  split_runs(all_runs, nullptr, m->sms, all_segs, nullptr, all_off);
+  split_runs(all_runs, nullptr, m->sms, 0.0, all_segs, nullptr, all_off);
   m->all_ctas = (int)all_off.size() - 1;
   int rc;
   if ((rc = upload_vec(&m->d_all_segs, all_segs)) != VFE_OK) return rc;
   if ((rc = upload_vec(&m->d_all_off, all_off)) != VFE_OK) return rc;
   if (m->stencil_on) {
-    split_runs(el_runs, nullptr, m->sms, m->segs, nullptr, m->seg_off);
-    split_runs(st_runs, &st_rmat, m->sms, m->st_segs, &m->st_mat, m->st_off);
+    split_runs(el_runs, nullptr, m->sms, 2.0, m->segs, nullptr, m->seg_off);
+    split_runs(st_runs, &st_rmat, m->sms, 0.0, m->st_segs, &m->st_mat, m->st_off);
   } else {
     m->segs = all_segs;
     m->seg_off = all_off;
@@ -1531,6 +1544,97 @@ CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v
 }
 
 extern "C" {
+
+int vfe_get_source_scale(vfe_mesh *m, double *dt2_over_m) {
+  if (!m || !dt2_over_m) return fail(VFE_EINVAL, "NULL argument");
+  *dt2_over_m = m->has_src ? m->src_scale : 0.0;
+  return VFE_OK;
+}
+
+int vfe_set_source_bound(vfe_mesh *m, const double dir[3], double f0_hz, double t0_s, double amp,
+                         double dt2_over_m) {
+  if (!m || !dir) return fail(VFE_EINVAL, "NULL argument");
+  if (m->has_src) return fail(VFE_ESTATE, "the mesh holds the source itself");
+  if (!(f0_hz > 0.0) || !std::isfinite(f0_hz) || !std::isfinite(amp) || !std::isfinite(t0_s) ||
+      !(dt2_over_m >= 0.0) || !std::isfinite(dt2_over_m))
+    return fail(VFE_EINVAL, "need f0 > 0, dt2_over_m >= 0 and finite t0, amp");
+  if (!std::isfinite(dir[0]) || !std::isfinite(dir[1]) || !std::isfinite(dir[2]))
+    return fail(VFE_EINVAL, "dir has non-finite components");
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  m->src_bound_only = m->opt.path == VFE_PATH_TC;  // the FP64 path has no scale
+  for (int c = 0; c < 3; ++c) m->src_dir[c] = dir[c];
+  m->f0 = f0_hz;
+  m->t0 = t0_s > 0.0 ? t0_s : 1.0 / f0_hz;
+  m->amp = amp;
+  m->src_scale = dt2_over_m;
+  invalidate_graphs(m);
+  return VFE_OK;
+}
+
+static unsigned long long *next_bound_word(vfe_mesh *m) {
+  return m->d_or + (size_t)((m->steps + 2) % 3) * (1 + m->tiles_x * m->tiles_y);
+}
+
+int vfe_get_scale_bound(vfe_mesh *m, unsigned long long *dev_word) {
+  if (!m || !dev_word) return fail(VFE_EINVAL, "NULL argument");
+  cudaSetDevice(m->device);
+  if (m->opt.path == VFE_PATH_TC)
+    CUDA_TRY(cudaMemcpyAsync(dev_word, next_bound_word(m), sizeof(unsigned long long),
+                             cudaMemcpyDeviceToDevice, m->stream));
+  else
+    CUDA_TRY(cudaMemsetAsync(dev_word, 0, sizeof(unsigned long long), m->stream));
+  return VFE_OK;
+}
+
+int vfe_set_scale_bound(vfe_mesh *m, const unsigned long long *dev_word) {
+  if (!m || !dev_word) return fail(VFE_EINVAL, "NULL argument");
+  cudaSetDevice(m->device);
+  if (m->opt.path == VFE_PATH_TC)
+    CUDA_TRY(cudaMemcpyAsync(next_bound_word(m), dev_word, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToDevice, m->stream));
+  return VFE_OK;
+}
+
+int vfe_plane_values(vfe_mesh *m, int64_t *n_values) {
+  if (!m || !n_values) return fail(VFE_EINVAL, "NULL argument");
+  *n_values = 3 * (int64_t)(m->nx + 1) * (m->ny + 1);
+  return VFE_OK;
+}
+
+int vfe_pack_plane(vfe_mesh *m, int k, double *dev_out) {
+  if (!m || !dev_out) return fail(VFE_EINVAL, "NULL argument");
+  if (k < 0 || k > m->nz) return fail(VFE_EINVAL, "node plane %d outside [0, %d]", k, m->nz);
+  if (m->damped) return fail(VFE_ESTATE, "plane exchange is not combined with damping");
+  cudaSetDevice(m->device);
+  const int64_t np = (int64_t)(m->nx + 1) * (m->ny + 1);
+  if (m->opt.path == VFE_PATH_TC) {
+    CUDA_TRY(slab_pack_tc(m->stream, m->d_U[m->cur], m->nx, m->ny, m->nxp, m->plane, m->comp, k,
+                          m->d_tcpersist, dev_out));
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(dev_out, m->d_u[m->cur] + 3 * np * k, sizeof(double) * 3 * np,
+                             cudaMemcpyDeviceToDevice, m->stream));
+  }
+  return VFE_OK;
+}
+
+int vfe_unpack_plane(vfe_mesh *m, int k, const double *dev_in) {
+  if (!m || !dev_in) return fail(VFE_EINVAL, "NULL argument");
+  if (k < 0 || k > m->nz) return fail(VFE_EINVAL, "node plane %d outside [0, %d]", k, m->nz);
+  if (m->damped) return fail(VFE_ESTATE, "plane exchange is not combined with damping");
+  cudaSetDevice(m->device);
+  const int64_t np = (int64_t)(m->nx + 1) * (m->ny + 1);
+  if (m->opt.path == VFE_PATH_TC) {
+    // the bound records the next step reads
+    unsigned long long *slot = next_bound_word(m);
+    CUDA_TRY(slab_unpack_tc(m->stream, m->d_U[m->cur], m->nx, m->ny, m->nxp, m->plane, m->comp, k,
+                            m->d_tcpersist, dev_in, slot, m->tiles_x));
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(m->d_u[m->cur] + 3 * np * k, dev_in, sizeof(double) * 3 * np,
+                             cudaMemcpyDeviceToDevice, m->stream));
+  }
+  return VFE_OK;
+}
 
 int vfe_debug_stencil_partials(vfe_mesh *m, const double *u, int64_t *out, int8_t *covered,
                                int *shift_out, int *frac_bits_out) {

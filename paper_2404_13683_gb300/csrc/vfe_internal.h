@@ -210,6 +210,12 @@ cudaError_t tc_launch_prologue_ex(cudaStream_t s, TcStepParams *params, int64_t 
 cudaError_t tc_launch_step(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
 cudaError_t tc_launch_batch_prologue(cudaStream_t s, const TcPrologueArgs *args, int n_meshes);
 cudaError_t tc_launch_batch_step(cudaStream_t s, const TcBatch &b, int stages);
+// node-plane exchange of the z-slab decomposition (vfe_slab.cu)
+cudaError_t slab_pack_tc(cudaStream_t s, const int64_t *U, int nx, int ny, int nxp, int64_t plane,
+                         int64_t comp, int k, const int64_t *persist, double *out);
+cudaError_t slab_unpack_tc(cudaStream_t s, int64_t *U, int nx, int ny, int nxp, int64_t plane,
+                           int64_t comp, int k, const int64_t *persist, const double *in,
+                           unsigned long long *slot, int tiles_x);
 cudaError_t stencil_prepare();
 // the node-stencil kernel over d.segs / d.seg_off / d.seg_mat (d.n_ctas CTAs;
 // nothing is launched for 0); tmap: box ST_BOXX x ST_BOXY x 1 x 3

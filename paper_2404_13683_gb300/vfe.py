@@ -36,6 +36,8 @@ EXPORTS = (
     "vfe_create_batch", "vfe_batch_step", "vfe_batch_synchronize", "vfe_destroy_batch",
     "vfe_misfit_gradient", "vfe_step_forced", "vfe_set_damping", "vfe_rayleigh_coefficients",
     "vfe_get_trace_rows_async", "vfe_debug_inject_status", "vfe_debug_stencil_partials",
+    "vfe_plane_values", "vfe_pack_plane", "vfe_unpack_plane", "vfe_get_scale_bound",
+    "vfe_set_scale_bound", "vfe_get_source_scale", "vfe_set_source_bound",
 )
 
 
@@ -101,6 +103,13 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_last_error.restype = ctypes.c_char_p
     L.vfe_debug_tc_partials.argtypes = [P, P, I, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
     L.vfe_debug_inject_status.argtypes = [P, I]
+    L.vfe_plane_values.argtypes = [P, ctypes.POINTER(I64)]
+    L.vfe_pack_plane.argtypes = [P, I, P]
+    L.vfe_unpack_plane.argtypes = [P, I, P]
+    L.vfe_get_scale_bound.argtypes = [P, P]
+    L.vfe_set_scale_bound.argtypes = [P, P]
+    L.vfe_get_source_scale.argtypes = [P, ctypes.POINTER(D)]
+    L.vfe_set_source_bound.argtypes = [P, P, D, D, D, D]
     L.vfe_debug_stencil_partials.argtypes = [P, P, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
     for name in EXPORTS:
         if name not in ("vfe_default_options", "vfe_last_error"):
@@ -304,6 +313,42 @@ def vfe_debug_stencil_partials(mesh, u):
     _check(load().vfe_debug_stencil_partials(mesh, _p(u), _p(out), _p(cov), ctypes.byref(sh),
                                              ctypes.byref(F)))
     return out, cov.astype(bool), sh.value, F.value
+
+
+def vfe_plane_values(mesh):
+    n = ctypes.c_int64()
+    _check(load().vfe_plane_values(mesh, ctypes.byref(n)))
+    return n.value
+
+
+def vfe_pack_plane(mesh, k, dev_ptr):
+    """Queue the copy of u^n of node plane k to the device address dev_ptr."""
+    _check(load().vfe_pack_plane(mesh, int(k), ctypes.c_void_p(int(dev_ptr))))
+
+
+def vfe_unpack_plane(mesh, k, dev_ptr):
+    """Queue the write of the device array at dev_ptr into u^n of plane k."""
+    _check(load().vfe_unpack_plane(mesh, int(k), ctypes.c_void_p(int(dev_ptr))))
+
+
+def vfe_get_scale_bound(mesh, dev_ptr):
+    _check(load().vfe_get_scale_bound(mesh, ctypes.c_void_p(int(dev_ptr))))
+
+
+def vfe_set_scale_bound(mesh, dev_ptr):
+    _check(load().vfe_set_scale_bound(mesh, ctypes.c_void_p(int(dev_ptr))))
+
+
+def vfe_get_source_scale(mesh):
+    v = ctypes.c_double()
+    _check(load().vfe_get_source_scale(mesh, ctypes.byref(v)))
+    return v.value
+
+
+def vfe_set_source_bound(mesh, direction, f0, t0, amp, dt2_over_m):
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    _check(load().vfe_set_source_bound(mesh, _p(d), float(f0), float(t0), float(amp),
+                                       float(dt2_over_m)))
 
 
 def vfe_create_batch(handles):
