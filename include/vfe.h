@@ -280,6 +280,19 @@ int vfe_debug_inject_status(vfe_mesh *mesh, int bits);
 int vfe_misfit_gradient(vfe_mesh *mesh, int nsteps, const double *data, int checkpoint_every,
                         double *grad_G, double *misfit);
 
+/* Per-element shear moduli (the parameters of the internal-structure
+ * estimation use, Section 1): element e gets shear modulus G[e] (Pa, host
+ * array of nx*ny*nz; entries of void cells are ignored) at the bulk modulus
+ * and density of its material, so that K_e = kappa K_e(1, 0) + G_e K_e(0, 1)
+ * in the element's closed form (Eq. OVFEMstiff; the trilinear element
+ * likewise).  G = NULL returns to the materials' moduli.  Takes effect from
+ * the next step; the time step is kept: VFE_EINVAL if it exceeds the
+ * stability limit with the largest G of some material, or for a negative or
+ * non-finite G.  Meshes with per-element moduli use the element-by-element
+ * kernel on every plane.  vfe_misfit_gradient then differentiates with
+ * respect to these moduli.  Synchronous. */
+int vfe_set_shear_moduli(vfe_mesh *mesh, const double *G);
+
 /* Batches: many meshes advanced together (the paper's many-case use, Section 1).
  * vfe_create_batch takes n distinct meshes on the tensor-core path, on one
  * device and with the same digit stage count; it keeps pointers to them (they

@@ -147,6 +147,11 @@ struct vfe_mesh {
   std::vector<int64_t> rec_nodes;
   std::vector<int32_t> rec_ijk;
 
+  // per-element shear moduli (vfe_set_shear_moduli)
+  bool elem_g = false;
+  std::vector<double> elem_G;
+  int64_t *d_elemB = nullptr;             // TC: round(G_e ds/384 2^e_ref)
+  double *d_elemG = nullptr, *d_kappa = nullptr, *d_Kkg = nullptr;  // FP64 path
   bool has_src = false;
   bool src_bound_only = false;  // the source lies in another slab: it only
                                 // enters the choice of the fixed-point scale
@@ -242,6 +247,7 @@ static TcDevice tc_device(const vfe_mesh *m, int cur) {
   d.src_node = m->has_src ? tc_index(m, m->src_node) : -1;
   d.traces = m->d_traces; d.or_slots = m->d_or; d.status = m->d_status;
   d.tiles_x = m->tiles_x; d.tiles_y = m->tiles_y;
+  d.elem_B = m->elem_g ? m->d_elemB : nullptr;
   d.params = m->d_tcparams;
   d.inj = m->d_inj;
   d.damped = m->damped ? 1 : 0;
@@ -281,6 +287,9 @@ static F64Device f64_device(const vfe_mesh *m, int cur) {
   d.src_node = m->has_src ? m->src_node : -1;
   d.inj = m->d_inj;
   d.damped = m->damped ? 1 : 0;
+  d.elem_G = m->elem_g ? m->d_elemG : nullptr;
+  d.kappa = m->d_kappa;
+  d.Kkg = m->d_Kkg;
   d.w = m->d_w[cur];
   d.w_next = m->d_w[1 - cur];
   d.da = 0.5 * m->alpha * m->dt;
@@ -386,7 +395,8 @@ int vfe_destroy(vfe_mesh *m) {
                   m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist, m->d_segs,
                   m->d_seg_off, m->d_inj, m->d_force, m->d_w[0], m->d_w[1],
                   m->d_W[0], m->d_W[1], m->d_all_segs, m->d_all_off, m->d_st_segs,
-                  m->d_st_mat, m->d_st_off, m->d_Bst};
+                  m->d_st_mat, m->d_st_off, m->d_Bst, m->d_elemB, m->d_elemG, m->d_kappa,
+                  m->d_Kkg};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -658,7 +668,7 @@ static int upload_vec(T **dptr, const std::vector<T> &v) {
 static int build_segments(vfe_mesh *m) {
   const int nx = m->nx, ny = m->ny, nz = m->nz, TX = m->tiles_x, TY = m->tiles_y;
   const int planes = nz + 1;
-  m->stencil_on = m->opt.path == VFE_PATH_TC && m->opt.stencil != 0 && !m->damped;
+  m->stencil_on = m->opt.path == VFE_PATH_TC && m->opt.stencil != 0 && !m->damped && !m->elem_g;
   std::vector<int4> all_runs, el_runs, st_runs;
   std::vector<int32_t> st_rmat;
   std::vector<char> forced((size_t)TX * TY * planes, 0);
@@ -1545,6 +1555,90 @@ CUresult vfe_encode_state_map(CUtensorMap *map, void *base, const VfeMeshView &v
 
 extern "C" {
 
+// the TC path's material unit e_ref and multipliers for the largest of the
+// bulk and shear terms (per material, and per element when elem_g)
+static int tc_encode_moduli(vfe_mesh *m) {
+  double mx = 0.0;
+  for (int i = 0; i < m->n_mat; ++i)
+    mx = std::max(mx, std::max(m->kappa[i] * m->h / 256.0, m->G[i] * m->h / 384.0));
+  if (m->elem_g)
+    for (int64_t e = 0; e < m->ne; ++e)
+      if (m->mat[e] >= 0) mx = std::max(mx, m->elem_G[e] * m->h / 384.0);
+  const int e_ref = 60 - std::ilogb(mx);
+  std::vector<TcMaterial> mats(m->n_mat);
+  for (int i = 0; i < m->n_mat; ++i) {
+    mats[i].A = llrint(std::ldexp(m->kappa[i] * m->h / 256.0, e_ref));
+    mats[i].B = llrint(std::ldexp(m->G[i] * m->h / 384.0, e_ref));
+    mats[i].shift = 0;
+    mats[i].pad = 0;
+  }
+  CUDA_TRY(cudaMemcpy(m->d_mats, mats.data(), sizeof(TcMaterial) * mats.size(),
+                      cudaMemcpyHostToDevice));
+  if (m->elem_g) {
+    std::vector<int64_t> B(m->ne, 0);
+    for (int64_t e = 0; e < m->ne; ++e)
+      if (m->mat[e] >= 0) B[e] = llrint(std::ldexp(m->elem_G[e] * m->h / 384.0, e_ref));
+    if (!m->d_elemB) CUDA_TRY(cudaMalloc(&m->d_elemB, sizeof(int64_t) * m->ne));
+    CUDA_TRY(cudaMemcpy(m->d_elemB, B.data(), sizeof(int64_t) * m->ne, cudaMemcpyHostToDevice));
+  }
+  m->e_ref = e_ref;
+  const int64_t pe = m->eC + m->e_ref;  // the exponent the step prologue reads
+  CUDA_TRY(cudaMemcpy(m->d_tcpersist + 4, &pe, sizeof(int64_t), cudaMemcpyHostToDevice));
+  return VFE_OK;
+}
+
+int vfe_set_shear_moduli(vfe_mesh *m, const double *G) {
+  if (!m) return fail(VFE_EINVAL, "mesh is NULL");
+  cudaSetDevice(m->device);
+  CUDA_TRY(cudaStreamSynchronize(m->stream));
+  if (G) {
+    for (int64_t e = 0; e < m->ne; ++e)
+      if (m->mat[e] >= 0 && !(G[e] >= 0.0 && std::isfinite(G[e])))
+        return fail(VFE_EINVAL, "G[%lld] must be finite and >= 0", (long long)e);
+    // stability with the largest shear modulus of each material (lambda_max of
+    // M_e^-1 K_e grows with G at fixed kappa)
+    std::vector<double> gmax(m->n_mat, -1.0);
+    for (int64_t e = 0; e < m->ne; ++e)
+      if (m->mat[e] >= 0) gmax[m->mat[e]] = std::max(gmax[m->mat[e]], G[e]);
+    double dtc = -1.0;
+    for (int i = 0; i < m->n_mat; ++i) {
+      if (gmax[i] < 0.0) continue;
+      double K[576];
+      element_matrix(m->opt.element_kind, m->h, m->kappa[i] - 2.0 * gmax[i] / 3.0, gmax[i], K);
+      const double lmax = max_eigenvalue(K) / (m->rho[i] * m->h * m->h * m->h / 8.0);
+      const double c = lmax > 0.0 ? 2.0 / std::sqrt(lmax) : 1e300;
+      if (dtc < 0.0 || c < dtc) dtc = c;
+    }
+    if (dtc > 0.0 && m->dt > dtc)
+      return fail(VFE_EINVAL, "dt %g exceeds the stability limit %g with these moduli", m->dt, dtc);
+    m->elem_G.assign(G, G + m->ne);
+    m->elem_g = true;
+    if (dtc > 0.0) m->dt_crit = dtc;
+  } else {
+    m->elem_g = false;
+    m->elem_G.clear();
+  }
+  if (m->opt.path == VFE_PATH_TC) {
+    const int rc = tc_encode_moduli(m);
+    if (rc != VFE_OK) return rc;
+  } else if (m->elem_g) {
+    std::vector<double> Kkg(2 * 576), gE(m->elem_G);
+    element_matrix(m->opt.element_kind, m->h, 1.0, 0.0, Kkg.data());
+    element_matrix(m->opt.element_kind, m->h, -2.0 / 3.0, 1.0, Kkg.data() + 576);
+    for (int64_t e = 0; e < m->ne; ++e)
+      if (m->mat[e] < 0) gE[e] = 0.0;
+    if (!m->d_elemG) CUDA_TRY(cudaMalloc(&m->d_elemG, sizeof(double) * m->ne));
+    if (!m->d_kappa) CUDA_TRY(cudaMalloc(&m->d_kappa, sizeof(double) * m->n_mat));
+    if (!m->d_Kkg) CUDA_TRY(cudaMalloc(&m->d_Kkg, sizeof(double) * 2 * 576));
+    CUDA_TRY(cudaMemcpy(m->d_elemG, gE.data(), sizeof(double) * m->ne, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->d_kappa, m->kappa.data(), sizeof(double) * m->n_mat,
+                        cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(m->d_Kkg, Kkg.data(), sizeof(double) * 2 * 576, cudaMemcpyHostToDevice));
+  }
+  invalidate_graphs(m);
+  return rebuild_work(m);  // per-element moduli: the element kernel everywhere
+}
+
 int vfe_get_source_scale(vfe_mesh *m, double *dt2_over_m) {
   if (!m || !dt2_over_m) return fail(VFE_EINVAL, "NULL argument");
   *dt2_over_m = m->has_src ? m->src_scale : 0.0;
@@ -2193,6 +2287,7 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
                               m->n_mat, &o, &adj)) != VFE_OK)
       break;
     if ((rc = vfe_set_receivers(adj, nr, m->rec_ijk.data())) != VFE_OK) break;
+    if (m->elem_g && (rc = vfe_set_shear_moduli(adj, m->elem_G.data())) != VFE_OK) break;
     // forward from rest with checkpoints every C steps
     if ((rc = rewind_mesh(m)) != VFE_OK) break;
     if ((rc = ensure_trace_capacity(m, N)) != VFE_OK) break;

@@ -51,7 +51,11 @@ __global__ void f64_prologue_kernel(F64StepParams *p, int64_t *persist, TcSource
 template <int MODE>
 __global__ void __launch_bounds__(256) f64_step_kernel(const F64Device d, const F64StepParams *pp) {
   extern __shared__ double sK[];
-  for (int i = threadIdx.x; i < d.n_mat * 576; i += blockDim.x) sK[i] = d.K[i];
+  // per-material element matrices, or Kk, Kg with per-element shear moduli
+  const bool per_elem = d.elem_G != nullptr;
+  const int nK = per_elem ? 2 * 576 : d.n_mat * 576;
+  const double *Ksrc = per_elem ? d.Kkg : d.K;
+  for (int i = threadIdx.x; i < nK; i += blockDim.x) sK[i] = Ksrc[i];
   __syncthreads();
   const int nx = d.nx, ny = d.ny, nz = d.nz;
   const int64_t sx = nx + 1, sxy = (int64_t)(nx + 1) * (ny + 1);
@@ -63,8 +67,30 @@ __global__ void __launch_bounds__(256) f64_step_kernel(const F64Device d, const 
     for (int a = 0; a < 8; ++a) {
       const int ex = ni - (a & 1), ey = nj - ((a >> 1) & 1), ez = nk - (a >> 2);
       if (ex < 0 || ey < 0 || ez < 0 || ex >= nx || ey >= ny || ez >= nz) continue;
-      const int m = d.mat[(int64_t)ex + (int64_t)nx * ((int64_t)ey + (int64_t)ny * ez)];
+      const int64_t e = (int64_t)ex + (int64_t)nx * ((int64_t)ey + (int64_t)ny * ez);
+      const int m = d.mat[e];
       if (m < 0) continue;
+      if (per_elem) {  // kappa_m (Kk u_e) + G_e (Kg u_e)
+        const double *Kk = sK + (3 * a) * 24, *Kg = sK + 576 + (3 * a) * 24;
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0, h0 = 0.0, h1 = 0.0, h2 = 0.0;
+        for (int b = 0; b < 8; ++b) {
+          const int64_t nb = (ex + (b & 1)) + sx * (ey + ((b >> 1) & 1)) + sxy * (ez + (b >> 2));
+          const double u0 = x[3 * nb], u1 = x[3 * nb + 1], u2 = x[3 * nb + 2];
+          const double *k0 = Kk + 3 * b, *k1 = Kk + 24 + 3 * b, *k2 = Kk + 48 + 3 * b;
+          g0 = fma(k0[0], u0, fma(k0[1], u1, fma(k0[2], u2, g0)));
+          g1 = fma(k1[0], u0, fma(k1[1], u1, fma(k1[2], u2, g1)));
+          g2 = fma(k2[0], u0, fma(k2[1], u1, fma(k2[2], u2, g2)));
+          const double *q0 = Kg + 3 * b, *q1 = Kg + 24 + 3 * b, *q2 = Kg + 48 + 3 * b;
+          h0 = fma(q0[0], u0, fma(q0[1], u1, fma(q0[2], u2, h0)));
+          h1 = fma(q1[0], u0, fma(q1[1], u1, fma(q1[2], u2, h1)));
+          h2 = fma(q2[0], u0, fma(q2[1], u1, fma(q2[2], u2, h2)));
+        }
+        const double kap = d.kappa[m], G = d.elem_G[e];
+        f0 = fma(kap, g0, fma(G, h0, f0));
+        f1 = fma(kap, g1, fma(G, h1, f1));
+        f2 = fma(kap, g2, fma(G, h2, f2));
+        continue;
+      }
       const double *K = sK + m * 576 + (3 * a) * 24;
       for (int b = 0; b < 8; ++b) {
         const int64_t nb = (ex + (b & 1)) + sx * (ey + ((b >> 1) & 1)) + sxy * (ez + (b >> 2));
@@ -122,7 +148,7 @@ cudaError_t f64_prepare() {
 
 template <int MODE>
 static cudaError_t f64_launch(cudaStream_t s, const F64Device &d, const F64StepParams *pp) {
-  const int smem = d.n_mat * 576 * (int)sizeof(double);
+  const int smem = (d.elem_G ? 2 : d.n_mat) * 576 * (int)sizeof(double);
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

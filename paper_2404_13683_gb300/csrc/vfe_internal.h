@@ -106,6 +106,9 @@ struct TcDevice {         // everything the TC kernels read (by value)
   // and its B operand image (9 neighbour rows x 16 x 16 fp16)
   const int32_t *seg_mat;
   const uint16_t *Bst;
+  // per-element shear modulus (vfe_set_shear_moduli): the element kernel's
+  // G multiplier round(G_e ds/384 2^e_ref) per element, or nullptr
+  const int64_t *elem_B;
 };
 
 // Several meshes advanced by one launch: each segment belongs to one mesh,
@@ -154,6 +157,11 @@ struct F64Device {
   const double *inj;      // [rows][n_rec][3] displacement increments at the receivers
   // Rayleigh damping (damped != 0): K acts on w^n = u^n + b (u^n - u^{n-1});
   // (1 + a) u^{n+1} = 2 u^n - (1 - a) u^{n-1} + dt^2/m (F - K w^n)
+  // per-element shear modulus (elem_G != nullptr): K_e = kappa_m Kk + G_e Kg
+  // with Kk = K_e(kappa = 1, G = 0), Kg = K_e(kappa = 0, G = 1) of the element kind
+  const double *elem_G;   // per element
+  const double *kappa;    // per material
+  const double *Kkg;      // Kk then Kg (2 x 576)
   const double *w;        // w^n [nn][3]
   double *w_next;         // w^{n+1}
   double da, db;          // a = alpha dt / 2, b = beta / dt

@@ -367,11 +367,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                  ? d.mat[(int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L)]
                  : -1;
     };
+    // per-element shear multiplier (meshes with per-element G), one layer ahead
+    auto elemB_at = [&](int L) -> int64_t {
+      return (d.elem_B && elem_xy && L >= 0 && L < d.nz)
+                 ? d.elem_B[(int64_t)gx + (int64_t)d.nx * ((int64_t)gy + (int64_t)d.ny * L)]
+                 : 0;
+    };
     int m_next = mat_at(Lfirst);
+    int64_t b_next = elemB_at(Lfirst);
     bool okp = true;  // plane waits of the previous layer's second phase
     for (int L = Lfirst; L <= Llast; ++L) {
       const int m = m_next;
       m_next = mat_at(L + 1);
+      const int64_t b_elem = b_next;
+      b_next = elemB_at(L + 1);
       int64_t uprev[3] = {0, 0, 0}, cn = 0, ucur_g[3] = {0, 0, 0};
       const bool upd = (MODE == TC_MODE_STEP) && updater && L >= Z0;
       const int64_t nidx = (int64_t)L * d.plane + (int64_t)gj * d.nxp + gi;
@@ -394,7 +403,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // (c) epilogue: per corner group (dy, dz), stages x 12 columns
       const TcMaterial mt = m >= 0 ? smat[m] : zero_mat;
       const int A1 = (int)(mt.A >> 31), A0 = (int)(mt.A & 0x7FFFFFFF);
-      const int B1 = (int)(mt.B >> 31), B0 = (int)(mt.B & 0x7FFFFFFF);
+      const int64_t mB = (d.elem_B && m >= 0) ? b_elem : mt.B;
+      const int B1 = (int)(mB >> 31), B0 = (int)(mB & 0x7FFFFFFF);
       const uint32_t tbase =
           tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * kTileCols);
       int64_t own[3] = {0, 0, 0};  // this half's (dy = 1) corner sums

@@ -38,6 +38,7 @@ EXPORTS = (
     "vfe_get_trace_rows_async", "vfe_debug_inject_status", "vfe_debug_stencil_partials",
     "vfe_plane_values", "vfe_pack_plane", "vfe_unpack_plane", "vfe_get_scale_bound",
     "vfe_set_scale_bound", "vfe_get_source_scale", "vfe_set_source_bound",
+    "vfe_set_shear_moduli",
 )
 
 
@@ -110,6 +111,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_set_scale_bound.argtypes = [P, P]
     L.vfe_get_source_scale.argtypes = [P, ctypes.POINTER(D)]
     L.vfe_set_source_bound.argtypes = [P, P, D, D, D, D]
+    L.vfe_set_shear_moduli.argtypes = [P, P]
     L.vfe_debug_stencil_partials.argtypes = [P, P, P, P, ctypes.POINTER(I), ctypes.POINTER(I)]
     for name in EXPORTS:
         if name not in ("vfe_default_options", "vfe_last_error"):
@@ -349,6 +351,18 @@ def vfe_set_source_bound(mesh, direction, f0, t0, amp, dt2_over_m):
     d = np.ascontiguousarray(direction, dtype=np.float64)
     _check(load().vfe_set_source_bound(mesh, _p(d), float(f0), float(t0), float(amp),
                                        float(dt2_over_m)))
+
+
+def vfe_set_shear_moduli(mesh, G):
+    """Per-element shear moduli (None: the materials' own)."""
+    if G is None:
+        _check(load().vfe_set_shear_moduli(mesh, None))
+        return
+    g = np.ascontiguousarray(G, dtype=np.float64).reshape(-1)
+    _, ne = vfe_get_sizes(mesh)
+    if g.size != ne:
+        raise ValueError("G must have one value per element")
+    _check(load().vfe_set_shear_moduli(mesh, _p(g)))
 
 
 def vfe_create_batch(handles):
