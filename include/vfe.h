@@ -66,6 +66,9 @@ typedef struct vfe_options {
                        Eq. GE:TC summed at the node, same integer split); 0
                        uses the element-by-element kernel everywhere.  The two
                        agree to the FP64-equivalent bound of the split. */
+  int ctas;         /* TC path: CTAs per kernel launch, i.e. how many pieces the
+                       (node column x plane range) work bricks are cut into;
+                       0 (default) = one per SM, the most the kernels take */
 } vfe_options;
 
 typedef struct vfe_mesh vfe_mesh;
@@ -116,7 +119,8 @@ int vfe_internal_force(vfe_mesh *mesh, const double *u, double *f);
 
 /* Advance n >= 0 central-difference steps (Eq. eqtimehistory):
  * u^{n+1} = 2u^n - u^{n-1} + dt^2 M^-1 (F^n - K u^n) on free DOFs.
- * Asynchronous on the mesh's stream (launched as a captured CUDA graph);
+ * Asynchronous on the mesh's stream (launched as captured CUDA graphs of 32
+ * and of 2 steps, so a long run pays the launch cost once per 32 steps);
  * device errors surface at the next synchronising call.  VFE_EINVAL: n < 0;
  * VFE_ENOMEM: growing the device trace buffer; VFE_ECUDA: a launch failed. */
 int vfe_step(vfe_mesh *mesh, int n);
@@ -295,10 +299,11 @@ int vfe_set_shear_moduli(vfe_mesh *mesh, const double *G);
 
 /* Batches: many meshes advanced together (the paper's many-case use, Section 1).
  * vfe_create_batch takes n distinct meshes on the tensor-core path, on one
- * device and with the same digit stage count; it keeps pointers to them (they
- * must outlive the batch).  vfe_batch_step(b, n) advances every mesh n steps
- * with one fused kernel launch per step over all meshes' node columns (plus
- * one per-step prologue launch), replayed as a captured CUDA graph; each mesh
+ * device; it keeps pointers to them (they must outlive the batch).  Meshes
+ * may differ in their digit stage count.  vfe_batch_step(b, n) advances every
+ * mesh n steps with one fused kernel launch per step and stage count over
+ * those meshes' node columns (plus one per-step prologue launch), replayed as
+ * captured CUDA graphs of 32 and of 2 steps; each mesh
  * keeps its own source, receivers, traces, state and time step.  Work queued
  * on a mesh's own stream before the call runs first; calls on a mesh after it
  * wait for the batch.  Changing a mesh's source or receivers between batch

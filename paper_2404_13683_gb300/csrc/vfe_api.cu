@@ -203,8 +203,10 @@ struct vfe_mesh {
   int e_ref = 0, eC = 0;
   double src_scale = 0.0;  // dt^2 / m at the source node
 
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};       // two steps from state parity p
   bool graph_valid[2] = {false, false};
+  cudaGraphExec_t graph_long[2] = {nullptr, nullptr};  // kLongSteps steps
+  bool graph_long_valid[2] = {false, false};
   int64_t gen = 0;  // bumped whenever kernel arguments change (batches rebuild)
   double *d_inj = nullptr;  // injection array [rows][n_rec][3] (adjoint source)
   double *d_force = nullptr;  // explicit force rows of vfe_step_forced [k][3], then one
@@ -219,8 +221,15 @@ static void invalidate_graphs(vfe_mesh *m) {
     if (m->graph[i]) cudaGraphExecDestroy(m->graph[i]);
     m->graph[i] = nullptr;
     m->graph_valid[i] = false;
+    if (m->graph_long[i]) cudaGraphExecDestroy(m->graph_long[i]);
+    m->graph_long[i] = nullptr;
+    m->graph_long_valid[i] = false;
   }
 }
+
+// steps per long graph: runs of many steps replay one graph of this many
+// steps (the launch cost of small meshes is paid once per graph, not per step)
+constexpr int kLongSteps = 32;
 
 static int64_t node_id(const vfe_mesh *m, int i, int j, int k) {
   return (int64_t)i + (int64_t)(m->nx + 1) * ((int64_t)j + (int64_t)(m->ny + 1) * k);
@@ -335,24 +344,37 @@ static int enqueue_step(vfe_mesh *m, int cur) {
   return VFE_OK;
 }
 
-static int ensure_graph(vfe_mesh *m, int cur) {
-  if (m->graph_valid[cur]) return VFE_OK;
+// a captured graph of `len` (even) steps from state parity cur
+static int capture_steps(vfe_mesh *m, int cur, int len, cudaGraphExec_t *out) {
   cudaGraph_t g = nullptr;
   CUDA_TRY(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_step(m, cur);
-  if (rc == VFE_OK) rc = enqueue_step(m, 1 - cur);
+  int rc = VFE_OK;
+  for (int k = 0; k < len && rc == VFE_OK; ++k) rc = enqueue_step(m, cur ^ (k & 1));
   cudaError_t e = cudaStreamEndCapture(m->stream, &g);
   if (rc != VFE_OK) {
     if (g) cudaGraphDestroy(g);
     return rc;
   }
   if (e != cudaSuccess) return fail(VFE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&m->graph[cur], g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess)
     return fail(VFE_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
-  m->graph_valid[cur] = true;
   return VFE_OK;
+}
+
+static int ensure_graph(vfe_mesh *m, int cur) {
+  if (m->graph_valid[cur]) return VFE_OK;
+  const int rc = capture_steps(m, cur, 2, &m->graph[cur]);
+  if (rc == VFE_OK) m->graph_valid[cur] = true;
+  return rc;
+}
+
+static int ensure_long_graph(vfe_mesh *m, int cur) {
+  if (m->graph_long_valid[cur]) return VFE_OK;
+  const int rc = capture_steps(m, cur, kLongSteps, &m->graph_long[cur]);
+  if (rc == VFE_OK) m->graph_long_valid[cur] = true;
+  return rc;
 }
 
 static int check_status(vfe_mesh *m) {
@@ -382,6 +404,7 @@ void vfe_default_options(vfe_options *o) {
   o->device = 0;
   o->stream = nullptr;
   o->stencil = 1;
+  o->ctas = 0;
 }
 
 int vfe_destroy(vfe_mesh *m) {
@@ -440,6 +463,7 @@ int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_id
   if (opt.fix_bottom < 0 || opt.fix_bottom > 2)
     return fail(VFE_EINVAL, "fix_bottom must be 0, 1 or 2");
   if (opt.stencil != 0 && opt.stencil != 1) return fail(VFE_EINVAL, "stencil must be 0 or 1");
+  if (opt.ctas < 0) return fail(VFE_EINVAL, "ctas must be >= 0");
 
   vfe_mesh *m = new vfe_mesh();
   m->nx = nx; m->ny = ny; m->nz = nz; m->h = h; m->opt = opt; m->device = opt.device;
@@ -618,7 +642,14 @@ static void split_runs(const std::vector<int4> &runs, const std::vector<int32_t>
     total += (r.w - r.z) + seg_cost;
     planes += r.w - r.z;
   }
-  const int64_t G = planes > 0 ? std::min<int64_t>(sms, planes) : 0;
+  // at least twice a segment's cost per range, so that a range's target
+  // exceeds what its first segment may take beyond it
+  const int64_t G = planes > 0 ? std::min<int64_t>(
+                                     std::min<int64_t>(sms, planes),
+                                     std::max<int64_t>(1, (int64_t)(total / (2.0 * (seg_cost + 1.0)))))
+                               : 0;
+  // a range boundary usually cuts a run, which adds a segment
+  if (G > 1) total += (double)(G - 1) * seg_cost;
   segs.clear();
   if (seg_mat) seg_mat->clear();
   off.assign(G + 1, 0);
@@ -721,16 +752,18 @@ static int build_segments(vfe_mesh *m) {
       }
       flush(planes);
     }
+  // CTAs per launch: one per SM unless the options ask for fewer
+  const int ctas = m->opt.ctas > 0 ? std::min(m->opt.ctas, m->sms) : m->sms;
   std::vector<int32_t> all_off;
   std::vector<int4> all_segs;
-  split_runs(all_runs, nullptr, m->sms, 0.0, all_segs, nullptr, all_off);
+  split_runs(all_runs, nullptr, ctas, 0.0, all_segs, nullptr, all_off);
   m->all_ctas = (int)all_off.size() - 1;
   int rc;
   if ((rc = upload_vec(&m->d_all_segs, all_segs)) != VFE_OK) return rc;
   if ((rc = upload_vec(&m->d_all_off, all_off)) != VFE_OK) return rc;
   if (m->stencil_on) {
-    split_runs(el_runs, nullptr, m->sms, 2.0, m->segs, nullptr, m->seg_off);
-    split_runs(st_runs, &st_rmat, m->sms, 0.0, m->st_segs, &m->st_mat, m->st_off);
+    split_runs(el_runs, nullptr, ctas, 2.0, m->segs, nullptr, m->seg_off);
+    split_runs(st_runs, &st_rmat, ctas, 0.0, m->st_segs, &m->st_mat, m->st_off);
   } else {
     m->segs = all_segs;
     m->seg_off = all_off;
@@ -1064,6 +1097,12 @@ static int run_steps(vfe_mesh *m, int n) {
   // pairs of steps replay a captured two-step graph; the source term, scales
   // and trace rows live in device memory, so the graph is reusable
   int64_t left = n;
+  while (left >= kLongSteps) {
+    rc = ensure_long_graph(m, m->cur);
+    if (rc != VFE_OK) return rc;
+    CUDA_TRY(cudaGraphLaunch(m->graph_long[m->cur], m->stream));
+    left -= kLongSteps;
+  }
   while (left >= 2) {
     rc = ensure_graph(m, m->cur);
     if (rc != VFE_OK) return rc;
@@ -1847,13 +1886,20 @@ struct vfe_batch {
   int64_t steps = 0;  // steps taken since the arrays were built
   std::vector<int4> segs;
   std::vector<int32_t> seg_mesh, seg_off;
+  // meshes grouped by digit stage count, one launch per group: its stage
+  // count, its CTAs, and where its CTA offsets start in seg_off
+  struct Group {
+    int stages, n_ctas, off_base;
+  };
+  std::vector<Group> groups;
   int4 *d_segs = nullptr;
   int32_t *d_seg_mesh = nullptr, *d_seg_off = nullptr, *d_recv_off = nullptr;
   TcRecv *d_recv = nullptr;
   TcDevice *d_devs[2] = {nullptr, nullptr};
   CUtensorMap *d_maps[2] = {nullptr, nullptr};
   TcPrologueArgs *d_pro = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};       // two steps from parity p
+  cudaGraphExec_t graph_long[2] = {nullptr, nullptr};  // kLongSteps steps
 };
 
 static void batch_free_arrays(vfe_batch *b) {
@@ -1867,6 +1913,8 @@ static void batch_free_arrays(vfe_batch *b) {
   for (int i = 0; i < 2; ++i) {
     if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
     b->graph[i] = nullptr;
+    if (b->graph_long[i]) cudaGraphExecDestroy(b->graph_long[i]);
+    b->graph_long[i] = nullptr;
   }
 }
 
@@ -1874,34 +1922,47 @@ static void batch_free_arrays(vfe_batch *b) {
 static int batch_build(vfe_batch *b) {
   batch_free_arrays(b);
   const int nm = (int)b->meshes.size();
-  // column-planes of all meshes in order, split into one equal range per SM
-  std::vector<int64_t> start(nm + 1, 0);
-  for (int i = 0; i < nm; ++i) {
-    const vfe_mesh *m = b->meshes[i];
-    start[i + 1] = start[i] + (int64_t)m->tiles_x * m->tiles_y * (m->nz + 1);
-  }
-  const int64_t total = start[nm];
-  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(b->sms, total));
   b->segs.clear();
   b->seg_mesh.clear();
-  b->seg_off.assign(G + 1, 0);
-  for (int64_t g = 0; g < G; ++g) {
-    b->seg_off[g] = (int32_t)b->segs.size();
-    int64_t lo = g * total / G;
-    const int64_t hi = (g + 1) * total / G;
-    while (lo < hi) {
-      int mi = (int)(std::upper_bound(start.begin(), start.end(), lo) - start.begin()) - 1;
-      const vfe_mesh *m = b->meshes[mi];
-      const int64_t planes = m->nz + 1, loc = lo - start[mi];
-      const int64_t col = loc / planes, z0 = loc % planes;
-      const int64_t z1 = std::min<int64_t>(planes, z0 + std::min(hi, start[mi + 1]) - lo);
-      b->segs.push_back(make_int4((int)(col % m->tiles_x), (int)(col / m->tiles_x), (int)z0,
-                                  (int)z1));
-      b->seg_mesh.push_back(mi);
-      lo += z1 - z0;
+  b->seg_off.clear();
+  b->groups.clear();
+  // per stage count (ascending), the column-planes of its meshes in order,
+  // split into one equal range per SM
+  for (int st = 1; st <= TC_MAX_STAGES; ++st) {
+    std::vector<int> idx;
+    for (int i = 0; i < nm; ++i)
+      if (b->meshes[i]->opt.stages == st) idx.push_back(i);
+    if (idx.empty()) continue;
+    std::vector<int64_t> start(idx.size() + 1, 0);
+    for (size_t q = 0; q < idx.size(); ++q) {
+      const vfe_mesh *m = b->meshes[idx[q]];
+      start[q + 1] = start[q] + (int64_t)m->tiles_x * m->tiles_y * (m->nz + 1);
     }
+    const int64_t total = start.back();
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(b->sms, total));
+    vfe_batch::Group grp;
+    grp.stages = st;
+    grp.n_ctas = (int)G;
+    grp.off_base = (int)b->seg_off.size();
+    for (int64_t g = 0; g < G; ++g) {
+      b->seg_off.push_back((int32_t)b->segs.size());
+      int64_t lo = g * total / G;
+      const int64_t hi = (g + 1) * total / G;
+      while (lo < hi) {
+        const int q = (int)(std::upper_bound(start.begin(), start.end(), lo) - start.begin()) - 1;
+        const vfe_mesh *m = b->meshes[idx[q]];
+        const int64_t planes = m->nz + 1, loc = lo - start[q];
+        const int64_t col = loc / planes, z0 = loc % planes;
+        const int64_t z1 = std::min<int64_t>(planes, z0 + std::min(hi, start[q + 1]) - lo);
+        b->segs.push_back(make_int4((int)(col % m->tiles_x), (int)(col / m->tiles_x), (int)z0,
+                                    (int)z1));
+        b->seg_mesh.push_back(idx[q]);
+        lo += z1 - z0;
+      }
+    }
+    b->seg_off.push_back((int32_t)b->segs.size());
+    b->groups.push_back(grp);
   }
-  b->seg_off[G] = (int32_t)b->segs.size();
   // receivers per batch segment (indices into each mesh's own trace rows)
   const int ns = (int)b->segs.size();
   std::vector<std::vector<TcRecv>> per(ns);
@@ -1991,22 +2052,25 @@ static int batch_build(vfe_batch *b) {
   return VFE_OK;
 }
 
-static TcBatch batch_args(const vfe_batch *b, int parity) {
+static TcBatch batch_args(const vfe_batch *b, int parity, const vfe_batch::Group &g) {
   TcBatch a;
   a.devs = b->d_devs[parity];
   a.maps = b->d_maps[parity];
   a.segs = b->d_segs;
   a.seg_mesh = b->d_seg_mesh;
-  a.seg_off = b->d_seg_off;
+  a.seg_off = b->d_seg_off + g.off_base;
   a.recv = b->d_recv;
   a.recv_off = b->d_recv_off;
-  a.n_ctas = (int)b->seg_off.size() - 1;
+  a.n_ctas = g.n_ctas;
   return a;
 }
 
+// one step of every mesh: the prologues, then one fused launch per group of
+// meshes with the same digit stage count
 static int batch_enqueue(vfe_batch *b, int parity) {
   CUDA_TRY(tc_launch_batch_prologue(b->stream, b->d_pro, (int)b->meshes.size()));
-  CUDA_TRY(tc_launch_batch_step(b->stream, batch_args(b, parity), b->stages));
+  for (const vfe_batch::Group &g : b->groups)
+    CUDA_TRY(tc_launch_batch_step(b->stream, batch_args(b, parity, g), g.stages));
   return VFE_OK;
 }
 
@@ -2024,9 +2088,6 @@ int vfe_create_batch(int n, vfe_mesh *const *meshes, vfe_batch **out) {
       return fail(VFE_EINVAL, "mesh %d is on another device", i);
     if (meshes[i]->damped)
       return fail(VFE_EINVAL, "mesh %d is damped: batches step undamped meshes only", i);
-    if (meshes[i]->opt.stages != meshes[0]->opt.stages)
-      return fail(VFE_EINVAL, "mesh %d uses %d digit stages, mesh 0 uses %d", i,
-                  meshes[i]->opt.stages, meshes[0]->opt.stages);
     for (int j = 0; j < i; ++j)
       if (meshes[j] == meshes[i]) return fail(VFE_EINVAL, "mesh %d appears twice", i);
   }
@@ -2088,23 +2149,39 @@ int vfe_batch_step(vfe_batch *b, int n) {
     int rc = batch_build(b);
     if (rc != VFE_OK) return rc;
   }
+  // runs of steps replay captured graphs of kLongSteps, then of 2 steps
+  auto capture = [&](int parity, int len, cudaGraphExec_t *out) -> int {
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = VFE_OK;
+    for (int k = 0; k < len && rc == VFE_OK; ++k) rc = batch_enqueue(b, parity ^ (k & 1));
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc != VFE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(VFE_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(VFE_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+    return VFE_OK;
+  };
   int64_t left = n;
+  while (left >= kLongSteps) {
+    const int parity = (int)(b->steps & 1);
+    if (!b->graph_long[parity]) {
+      const int rc = capture(parity, kLongSteps, &b->graph_long[parity]);
+      if (rc != VFE_OK) return rc;
+    }
+    CUDA_TRY(cudaGraphLaunch(b->graph_long[parity], b->stream));
+    b->steps += kLongSteps;
+    left -= kLongSteps;
+  }
   while (left >= 2) {
     const int parity = (int)(b->steps & 1);
     if (!b->graph[parity]) {
-      cudaGraph_t g = nullptr;
-      CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-      int rc = batch_enqueue(b, parity);
-      if (rc == VFE_OK) rc = batch_enqueue(b, 1 - parity);
-      cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-      if (rc != VFE_OK) {
-        if (g) cudaGraphDestroy(g);
-        return rc;
-      }
-      if (e != cudaSuccess) return fail(VFE_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&b->graph[parity], g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return fail(VFE_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+      const int rc = capture(parity, 2, &b->graph[parity]);
+      if (rc != VFE_OK) return rc;
     }
     CUDA_TRY(cudaGraphLaunch(b->graph[parity], b->stream));
     b->steps += 2;

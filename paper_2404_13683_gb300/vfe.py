@@ -52,7 +52,7 @@ class vfe_options(ctypes.Structure):
     _fields_ = [("element_kind", ctypes.c_int), ("path", ctypes.c_int), ("stages", ctypes.c_int),
                 ("fix_bottom", ctypes.c_int), ("dt", ctypes.c_double),
                 ("cfl_fraction", ctypes.c_double), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("stencil", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("stencil", ctypes.c_int), ("ctas", ctypes.c_int)]
 
 
 _lib = None
@@ -423,7 +423,7 @@ class Mesh:
 
     def __init__(self, workload, path=VFE_PATH_TC, kind=VFE_OVFEM, stages=5, dt=None,
                  fix_bottom=None, stream=None, device=0, source=True, receivers=True,
-                 stencil=True):
+                 stencil=True, ctas=0):
         nx, ny, nz = workload["shape"]
         if dt is None:
             dt = float(workload.get("dt", 0.0))
@@ -431,7 +431,8 @@ class Mesh:
             fix_bottom = workload.get("fix_bottom", 1)
         opt = vfe_default_options(element_kind=kind, path=path, stages=stages, dt=dt,
                                   fix_bottom=int(fix_bottom), device=device,
-                                  stream=stream or 0, stencil=1 if stencil else 0)
+                                  stream=stream or 0, stencil=1 if stencil else 0,
+                                  ctas=int(ctas))
         self.handle = vfe_create_mesh(nx, ny, nz, workload["h"], workload["material_ids"],
                                       workload["material_table"], opt)
         self.workload = workload
