@@ -189,6 +189,13 @@ int vfe_get_dt(vfe_mesh *mesh, double *dt);
 int vfe_get_sizes(vfe_mesh *mesh, int64_t *n_nodes, int64_t *n_elements);
 int vfe_get_step_count(vfe_mesh *mesh, int64_t *steps);
 
+/* Kernel launches one step enqueues on the mesh's stream: on the TC path the
+ * one-thread prologue, the element kernel (when any column-plane needs it)
+ * and the node-stencil kernel (when enabled and some column-plane is
+ * uniform); on the FP64 path the prologue and the step kernel.  VFE_EINVAL:
+ * a NULL argument. */
+int vfe_get_launches_per_step(vfe_mesh *mesh, int *launches);
+
 /* Read / replace the state (u^n, u^{n-1}) as FP64 [nodes][3] host arrays.
  * Values at fixed or massless nodes are forced to zero by vfe_set_state.
  * Both wait for the mesh's queued work.  VFE_EINVAL: a NULL argument, or

@@ -1231,6 +1231,15 @@ int vfe_get_step_count(vfe_mesh *m, int64_t *steps) {
   return VFE_OK;
 }
 
+int vfe_get_launches_per_step(vfe_mesh *m, int *launches) {
+  if (!m || !launches) return fail(VFE_EINVAL, "NULL argument");
+  if (m->opt.path == VFE_PATH_TC)
+    *launches = 1 + (tc_device(m, 0).n_ctas > 0 ? 1 : 0) + (m->stencil_on ? 1 : 0);
+  else
+    *launches = 2;
+  return VFE_OK;
+}
+
 }  // extern "C"
 
 // ---- state conversion (FP64 <-> fixed point for the TC path) -----------------

@@ -30,16 +30,18 @@
 // the B operand of input p starts at the rotation of its three blocks that
 // puts each output in its slot, so every MMA writes all 48 columns of the
 // ring and the z-sum of the stencil happens in TMEM.  A slot is read for
-// plane z once input z+1 is in, and the epilogue then writes the magic bias
-// 0x4B400000 (1.5 2^23) back into it, the start value for plane z+3; every
-// accumulator word is then 0x4B400000 + the exact integer.  Per input plane:
-// 3 dy x STAGES MMAs, each reading its 4 KB of digits once for three outputs.
+// plane z once input z+1 is in; before input z+2's MMAs add to it, an N = 16
+// MMA without accumulation writes the magic bias 0x4B400000 (1.5 2^23) into
+// it (constant K rows 12..15 of the digit block against a bias image), the
+// start value for plane z+3; every accumulator word is then 0x4B400000 + the
+// exact integer.  Per input plane: (1 + 3 dy) x STAGES MMAs, the dy ones
+// reading their 4 KB of digits once for three outputs.
 //
 // A CTA owns 15x15 node columns (the element path's partition) and computes
 // 16x16 (the 16th row and column are dropped), marching up in z through its
 // segment's planes: TMA brings node planes (box 20 x 18 x 1 x 3 int64) into an
-// 8-slot ring six planes ahead; per plane L the 8 epilogue warps read and
-// re-arm the TMEM slot of plane L, recombine and update node plane L while
+// 8-slot ring six planes ahead; per plane L the 8 epilogue warps read the
+// TMEM slot of plane L, recombine and update node plane L while
 // warp 8 issues the MMAs of input plane L+2 and warps 9-15 digitise plane L+3
 // (one CTA barrier per plane).  Source and receiver planes, mesh faces and
 // material interfaces are left to the element kernel (vfe_tc.cu).
@@ -70,16 +72,23 @@ constexpr int kUSlots = 8;
 constexpr int kBKStride = 10 * 128;
 constexpr int kBImage = 2 * kBKStride;                    // 2560
 constexpr int kBBytes = 9 * kBImage;
+// the bias image: 16 K rows x 16 N columns, K rows 12..15 = 12288 (fp16),
+// the rest zero; against the constant 256 in K rows 12..15 of every digit
+// block it gives 4 x 256 x 12288 = 1.5 2^23 in each of the 16 columns
+constexpr int kBiasBytes = 512;
 
 constexpr int kOffD = 0;
 constexpr int kOffU = kOffD + kDSlots * kDSlotBytes;
 constexpr int kOffB = kOffU + kUSlots * kUStride;
-constexpr int kOffBar = kOffB + kBBytes;
+constexpr int kOffBias = kOffB + kBBytes;
+constexpr int kOffBar = kOffBias + kBiasBytes;
 constexpr int kOffMisc = kOffBar + 16 * 8;
 constexpr int kSmemBytes = kOffMisc + 64;
 
 static_assert(kOffU % 128 == 0 && kUStride % 128 == 0, "TMA destinations 128-byte aligned");
-static_assert(kDSlotBytes % 256 == 0 && kOffB % 128 == 0 && kOffBar % 8 == 0, "alignment");
+static_assert(kDSlotBytes % 256 == 0 && kOffB % 128 == 0 && kOffBias % 128 == 0 &&
+                  kOffBar % 8 == 0,
+              "alignment");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 static_assert(kSmemBytes > 114 * 1024, "one CTA per SM (TMEM and the element kernel)");
 
@@ -95,6 +104,11 @@ static_assert(kThreads - kDigit0 >= kTasks, "one task per digitising thread");
 // kind::f16, D f32, A f16 MN-major, B f16 K-major, N = 48, M = 128
 constexpr uint32_t kIdescN48 =
     (1u << 4) | (1u << 15) | ((uint32_t)(48 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// the same with N = 16 (one ring slot)
+constexpr uint32_t kIdescN16 =
+    (1u << 4) | (1u << 15) | ((uint32_t)(16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t kHalf256 = 0x5C005C00u;    // two fp16 256.0
+constexpr uint32_t kHalf12288 = 0x72007200u;  // two fp16 12288.0
 
 }  // namespace
 
@@ -111,6 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char *digits = smem + kOffD;
   int64_t *uslot = reinterpret_cast<int64_t *>(smem + kOffU);
   unsigned char *bimg = smem + kOffB;
+  unsigned char *bias_img = smem + kOffBias;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..7 U slots, 8,9 TMEM bufs
   uint32_t *misc = reinterpret_cast<uint32_t *>(smem + kOffMisc);  // [0] tmem base, [1] abort
 
@@ -143,12 +158,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   for (int i = tid; i < kBBytes / 16; i += kThreads)
     reinterpret_cast<uint4 *>(bimg)[i] = reinterpret_cast<const uint4 *>(d.Bst)[i];
-  {  // the unused K rows 12..15 of every node row block: zero (B is zero
-     // there too; finite values keep the products zero)
+  {  // the unused K rows 12..15 of every node row block: the constant 256,
+     // which the stencil images meet with zeros and the bias image with
+     // 12288 (the digitisers never write these rows)
     const int nrow = kDSlots * TC_MAX_STAGES * kSY;
     for (int i = tid; i < 4 * nrow; i += kThreads)
       *reinterpret_cast<uint4 *>(digits + (i >> 2) * kRowBytes + 128 + (4 + (i & 3)) * 16) =
-          make_uint4(0u, 0u, 0u, 0u);
+          make_uint4(kHalf256, kHalf256, kHalf256, kHalf256);
+    // bias image, K-major core matrices: N groups at 128 B, K groups at 256 B;
+    // an N row holds 8 K values (16 bytes); K rows 12..15 are bytes 8..15 of
+    // the N rows of K group 1
+    for (int i = tid; i < kBiasBytes / 16; i += kThreads) {
+      const bool hi = i >= 16;  // K group 1
+      reinterpret_cast<uint4 *>(bias_img)[i] =
+          hi ? make_uint4(0u, 0u, kHalf12288, kHalf12288) : make_uint4(0u, 0u, 0u, 0u);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -275,7 +299,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     // above) into the rings of every stage, all issued by warp 8 (an issuing
     // warp stalls while the tensor pipe drains, so no other work waits behind
     // it).  The B start block (1 - p) mod 3 of the five stored blocks puts
-    // output z = p + o into slot z mod 3.  commit: one mbarrier arrival once
+    // output z = p + o into slot z mod 3.  Input p is the first to reach
+    // output p + 1: per stage, an N = 16 MMA without accumulation first
+    // writes the magic bias 1.5 2^23 into that slot (the constant K rows of
+    // the digit block against the bias image; the epilogue read the slot's
+    // previous plane before the barrier that precedes this issue, and MMAs of
+    // one thread run in issue order).  commit: one mbarrier arrival once
     // these and all earlier MMAs are done (batch b on mbarrier 8 + (b & 1)).
     auto issue_mma = [&](int p, int v, int commit_batch) {
       if (commit_batch >= 0) mma_out |= 1u << (commit_batch & 1);
@@ -284,9 +313,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int s0 = ((1 - p) % 3 + 3) % 3;
       const uint32_t bimg_base = smem_u32(bimg) + (uint32_t)(v * 3 * kBImage + s0 * 256);
+      const uint32_t next_slot = (uint32_t)(16 * (((p + 1) % 3 + 3) % 3));
+      const uint64_t bias_desc = make_sdesc(smem_u32(bias_img), 256, 128);
 #pragma unroll 1
       for (int st = s_lo; st < TC_MAX_STAGES; ++st) {
         const uint32_t dcol = tmem_base + (uint32_t)(st * kRingCols);
+        mma_f16_elect(dcol + next_slot,
+                      make_sdesc(smem_u32(dslot_of(p) + st * kStageBytes + kRowBytes), 128, 256),
+                      bias_desc, kIdescN16, 0u);
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
           const uint32_t a = smem_u32(dslot_of(p) + st * kStageBytes + (1 + dy) * kRowBytes);
@@ -297,28 +331,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (commit_batch >= 0) mma_commit_elect(&bars[8 + (commit_batch & 1)]);
     };
-    // the epilogue warps write the magic bias into their lane's 8 columns
-    // (node jnode) of ring slot `slot` of every stage (all three slots when
-    // slot < 0)
-    auto arm_slots = [&](int slot) {
-      if (!epi) return;
-      const uint32_t lanes = tmem_base + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(8 * jnode);
-#pragma unroll 1
-      for (int st = s_lo; st < TC_MAX_STAGES; ++st)
-        for (int k = slot < 0 ? 0 : slot; k <= (slot < 0 ? 2 : slot); ++k)
-          tmem_st8v(lanes + (uint32_t)(st * kRingCols + 16 * k), TC_MAGIC_BITS);
-      tmem_wait_st();
-    };
-
     // ---- segment prologue: TMA of planes Z0-1 .. Z0+5, digits of Z0-1 .. Z0+2,
-    // every ring slot armed, the MMAs of inputs Z0-1, Z0, Z0+1 (batch Z0+1)
+    // the MMAs of inputs Z0-1, Z0, Z0+1 (batch Z0+1; their bias MMAs start
+    // the slots of outputs Z0, Z0+1, Z0+2)
     for (int p = Z0 - 1; p <= min(Z0 + 5, Z1); ++p) issue_plane(p, 0);
     bool ok = true;
     for (int p = Z0 - 1; p <= min(Z0 + 2, Z1); ++p) ok = wait_plane(p, true) && ok;
     if (sync_abort(ok)) { aborted = true; break; }
     for (int p = Z0 - 1; p <= min(Z0 + 2, Z1); ++p)
       for (int t = tid; t < kTasks; t += kThreads) digitise_task(p, t);
-    arm_slots(-1);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -345,8 +366,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t uprev[3] = {nx_uprev[0], nx_uprev[1], nx_uprev[2]};
       const int64_t cn = nx_cn;
       load_update(L + 1);
-      // plane L is complete once batch L+1 (input L+1) is in: read its slot,
-      // then re-arm the slot for plane L+3
+      // plane L is complete once batch L+1 (input L+1) is in: read its slot
+      // (input L+2's bias MMA restarts it for plane L+3 after the barrier)
       const int bL = (L + 1) & 1;
       uint32_t w[TC_MAX_STAGES][8];
       if (epi) {
@@ -361,10 +382,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = s_lo; s < TC_MAX_STAGES; ++s) tmem_ld8(tb + (uint32_t)(s * kRingCols), w[s]);
 #pragma unroll
         for (int s = s_lo; s < TC_MAX_STAGES; ++s) tmem_wait_ld8(w[s]);
-        arm_slots(L % 3);
       }
       mma_phase ^= 1u << bL;
-      // (b) TMEM reads and re-arming done, digit writes visible to the tensor core
+      // (b) TMEM reads done, digit writes visible to the tensor core
       tc_fence_before();
       fence_async_smem();
       if (sync_abort(okp)) { aborted = true; break; }

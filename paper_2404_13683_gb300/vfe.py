@@ -31,6 +31,7 @@ EXPORTS = (
     "vfe_default_options", "vfe_create_mesh", "vfe_destroy", "vfe_set_source",
     "vfe_set_receivers", "vfe_internal_force", "vfe_step", "vfe_synchronize",
     "vfe_get_traces", "vfe_get_dt", "vfe_get_sizes", "vfe_get_step_count",
+    "vfe_get_launches_per_step",
     "vfe_get_state", "vfe_set_state", "vfe_last_error", "vfe_debug_tc_partials",
     "vfe_get_trace_rows", "vfe_internal_force_noalloc",
     "vfe_create_batch", "vfe_batch_step", "vfe_batch_synchronize", "vfe_destroy_batch",
@@ -98,6 +99,7 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.vfe_get_dt.argtypes = [P, ctypes.POINTER(D)]
     L.vfe_get_sizes.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
     L.vfe_get_step_count.argtypes = [P, ctypes.POINTER(I64)]
+    L.vfe_get_launches_per_step.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     L.vfe_get_state.argtypes = [P, P, P]
     L.vfe_set_state.argtypes = [P, P, P]
     L.vfe_last_error.argtypes = []
@@ -265,6 +267,12 @@ def vfe_get_dt(mesh):
 def vfe_get_step_count(mesh):
     v = ctypes.c_int64()
     _check(load().vfe_get_step_count(mesh, ctypes.byref(v)))
+    return v.value
+
+
+def vfe_get_launches_per_step(mesh):
+    v = ctypes.c_int()
+    _check(load().vfe_get_launches_per_step(mesh, ctypes.byref(v)))
     return v.value
 
 
