@@ -635,7 +635,8 @@ static int encode_state_tmap(const vfe_mesh *m, EncodeTiledFn enc, void *base, C
 // cut where a range is full, and every piece is a segment.
 static void split_runs(const std::vector<int4> &runs, const std::vector<int32_t> *run_mat,
                        int sms, double seg_cost, std::vector<int4> &segs,
-                       std::vector<int32_t> *seg_mat, std::vector<int32_t> &off) {
+                       std::vector<int32_t> *seg_mat, std::vector<int32_t> &off,
+                       int min_piece = 1) {
   double total = 0.0;
   int64_t planes = 0;
   for (const int4 &r : runs) {
@@ -668,6 +669,12 @@ static void split_runs(const std::vector<int4> &runs, const std::vector<int32_t>
           continue;
         }
         take = std::max<int64_t>(1, std::min<int64_t>(take, (int64_t)std::llround(room)));
+        // no piece, and no remainder, below min_piece planes (the runs
+        // themselves are at least that long)
+        const int64_t left = r.w - z;
+        take = std::min<int64_t>(std::max<int64_t>(take, min_piece), left);
+        if (left - take > 0 && left - take < min_piece)
+          take = left - min_piece >= min_piece ? left - min_piece : left;
       }
       segs.push_back(make_int4(r.x, r.y, (int)z, (int)(z + take)));
       if (seg_mat) seg_mat->push_back((*run_mat)[ri]);
@@ -732,11 +739,19 @@ static int build_segments(vfe_mesh *m) {
         layer[ez] = v;
       }
       int run_cls = -3, run_z0 = 0;
+      // a uniform run of one plane goes to the element kernel (the stencil
+      // kernel's segments own two planes or more); element runs that touch
+      // are merged
       auto flush = [&](int z1) {
-        if (run_cls == -2) el_runs.push_back(make_int4(tx, ty, run_z0, z1));
-        if (run_cls >= 0) {
+        if (run_cls >= 0 && z1 - run_z0 >= 2) {
           st_runs.push_back(make_int4(tx, ty, run_z0, z1));
           st_rmat.push_back(run_cls);
+        } else if (run_cls != -1 && run_cls != -3) {
+          if (!el_runs.empty() && el_runs.back().x == tx && el_runs.back().y == ty &&
+              el_runs.back().w == run_z0)
+            el_runs.back().w = z1;
+          else
+            el_runs.push_back(make_int4(tx, ty, run_z0, z1));
         }
       };
       for (int L = 0; L < planes; ++L) {
@@ -763,7 +778,7 @@ static int build_segments(vfe_mesh *m) {
   if ((rc = upload_vec(&m->d_all_off, all_off)) != VFE_OK) return rc;
   if (m->stencil_on) {
     split_runs(el_runs, nullptr, ctas, 2.0, m->segs, nullptr, m->seg_off);
-    split_runs(st_runs, &st_rmat, ctas, 0.0, m->st_segs, &m->st_mat, m->st_off);
+    split_runs(st_runs, &st_rmat, ctas, 0.0, m->st_segs, &m->st_mat, m->st_off, 2);
   } else {
     m->segs = all_segs;
     m->seg_off = all_off;

@@ -37,14 +37,19 @@
 // exact integer.  Per input plane: (1 + 3 dy) x STAGES MMAs, the dy ones
 // reading their 4 KB of digits once for three outputs.
 //
-// A CTA owns 15x15 node columns (the element path's partition) and computes
-// 16x16 (the 16th row and column are dropped), marching up in z through its
-// segment's planes: TMA brings node planes (box 20 x 18 x 1 x 3 int64) into an
-// 8-slot ring six planes ahead; per plane L the 8 epilogue warps read the
-// TMEM slot of plane L, recombine and update node plane L while
-// warp 8 issues the MMAs of input plane L+2 and warps 9-15 digitise plane L+3
-// (one CTA barrier per plane).  Source and receiver planes, mesh faces and
-// material interfaces are left to the element kernel (vfe_tc.cu).
+// A segment is a 15x15 node column (the element path's partition; the CTA
+// computes 16x16 nodes and drops the 16th row and column) over two or more
+// node planes.  A CTA marches up in z through its segments as one stream:
+// TMA brings node planes (box 20 x 18 x 1 x 3 int64) into an 8-slot ring up
+// to seven planes ahead, and the digits and MMAs of the next segment's first
+// planes are made while the current one finishes, so a segment boundary
+// costs no pipeline refill.  Per output plane the 8 epilogue warps read its
+// TMEM slot, recombine and update the node plane while warps 8 and 12-15
+// issue the MMAs of the next output's inputs (one digit stage each) and
+// warps 9-12 digitise the inputs of the
+// output after it (one CTA barrier per output plane).  Source and receiver
+// planes, mesh faces and material interfaces are left to the element kernel
+// (vfe_tc.cu).
 #include <cuda_fp16.h>
 
 #include <cstring>
@@ -81,7 +86,13 @@ constexpr int kOffD = 0;
 constexpr int kOffU = kOffD + kDSlots * kDSlotBytes;
 constexpr int kOffB = kOffU + kUSlots * kUStride;
 constexpr int kOffBias = kOffB + kBBytes;
-constexpr int kOffBar = kOffBias + kBiasBytes;
+// the CTA's first kSegCap segments, staged once per launch: column and
+// planes, material multipliers and digit shift (48 bytes each); later
+// segments are read from global memory where they are needed
+constexpr int kSegCap = 256;
+constexpr int kSegInfoBytes = 48;
+constexpr int kOffSeg = kOffBias + kBiasBytes;
+constexpr int kOffBar = kOffSeg + kSegCap * kSegInfoBytes;
 constexpr int kOffMisc = kOffBar + 16 * 8;
 constexpr int kSmemBytes = kOffMisc + 64;
 
@@ -97,7 +108,11 @@ constexpr int kTmemCols = 256;
 constexpr int kRingCols = 48;                 // one stage: slots of planes z mod 3
 constexpr int kTasks = kSY * 3 * 2;           // digitisation tasks per plane
 constexpr int kEpiWarps = 8;                  // warps 0-7: epilogue (lane quarter x node)
-constexpr int kMmaWarp = 8;                   // warp 8: MMA issue
+// MMA issue: one warp per digit stage, warps 8, 12, 13, 14, 15 (warps 12-15
+// have no or few digitisation tasks); stage s_lo + r from the warp of rank r
+__device__ __forceinline__ int mma_rank_of(int warp) {
+  return warp == 8 ? 0 : (warp >= 12 ? warp - 11 : -1);
+}
 constexpr int kDigit0 = 9 * 32;               // first digitising thread (warps 9-15)
 static_assert(kThreads - kDigit0 >= kTasks, "one task per digitising thread");
 
@@ -126,8 +141,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   int64_t *uslot = reinterpret_cast<int64_t *>(smem + kOffU);
   unsigned char *bimg = smem + kOffB;
   unsigned char *bias_img = smem + kOffBias;
+  int4 *seginfo = reinterpret_cast<int4 *>(smem + kOffSeg);  // 3 int4 per segment
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..7 U slots, 8,9 TMEM bufs
-  uint32_t *misc = reinterpret_cast<uint32_t *>(smem + kOffMisc);  // [0] tmem base, [1] abort
+  uint32_t *misc = reinterpret_cast<uint32_t *>(smem + kOffMisc);  // [0] tmem base, [1] abort, [2] copies issued
 
   const int tid = threadIdx.x;
   const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0), lane = tid & 31;
@@ -145,9 +161,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   // ---- one-time setup ------------------------------------------------------
   if (tid == 0) {
     misc[1] = 0;
+    misc[2] = 0;
     for (int i = 0; i < kUSlots; ++i) mbar_init(&bars[i], 1);
-    mbar_init(&bars[8], 1);
-    mbar_init(&bars[9], 1);
+    mbar_init(&bars[8], STAGES);  // one commit per issuing warp
+    mbar_init(&bars[9], STAGES);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -190,11 +207,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     return;
   }
 
-  uint32_t uphase = 0;
   uint32_t mma_phase = 0;  // parity per MMA mbarrier (bits 0, 1)
-  // copies and MMAs in flight (the same bookkeeping in every thread): on an
-  // abort the CTA waits, bounded, for them before freeing TMEM
-  uint32_t tma_out = 0, mma_out = 0;
+  // MMA batches in flight (the same bookkeeping in every thread): on an
+  // abort the CTA waits, bounded, for them and for its copies before freeing
+  // TMEM
+  uint32_t mma_out = 0;
   bool aborted = false;
   auto sync_abort = [&](bool ok) -> bool {
     if (!ok) atomicExch(&misc[1], 1u);
@@ -206,21 +223,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   // digit planes keep only stages s_lo..4: q' = sum of those digits
   const int lo_bits = TC_DIGIT_BITS * s_lo;
   const int64_t dbias_hi = (dbias >> lo_bits) << lo_bits;
-
   const int sbeg = d.seg_off[blockIdx.x], send = d.seg_off[blockIdx.x + 1];
-  for (int sg = sbeg; sg < send && !aborted; ++sg) {
-    const int4 seg = d.segs[sg];
-    const TcMaterial mt = d.mats[d.seg_mat[sg]];
-    const int A1 = (int)(mt.A >> 31), A0 = (int)(mt.A & 0x7FFFFFFF);
-    const int B1 = (int)(mt.B >> 31), B0 = (int)(mt.B & 0x7FFFFFFF);
-    const int X0 = TC_OWN * seg.x - 1, Y0 = TC_OWN * seg.y - 1;
-    const int Z0 = seg.z, Z1 = seg.w;  // owned node planes [Z0, Z1), 1 <= Z0 < Z1 <= nz
-    const int xbox = X0 & ~1, xo = X0 - xbox;
-    const int gi = X0 + xl, gj = Y0 + yl;
-    const bool own = epi && xl <= TC_OWN && yl <= TC_OWN && gi <= d.nx && gj <= d.ny;
 
-    // digit shift of this column (Eq. intscaling): the previous step's bound
-    // over the 3x3 columns around it, as in the element kernel
+  // digit shift of a segment's column (Eq. intscaling): the previous step's
+  // bound over the 3x3 columns around it, as in the element kernel
+  auto seg_shq_global = [&](int4 seg) -> int {
     int shq = P.shq;
     if (MODE == TC_MODE_STEP) {
       const unsigned long long *prev =
@@ -234,174 +241,316 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int b = o ? 64 - __clzll((long long)o) : 0;
       shq = min(P.shq, max(0, b - TC_QBITS));
     }
-    const int Rseg = P.eCref + P.rs - shq - 63;
-    unsigned long long or_seg = 0;
+    return shq;
+  };
+  // segment table entry: {tx, ty, z0, z1}, {A1, A0, B1, B0}, {shq, -, -, -}
+  auto seg_fill = [&](int sg, int4 *e) {
+    const int4 s = d.segs[sg];
+    const TcMaterial mt = d.mats[d.seg_mat[sg]];
+    e[0] = s;
+    e[1] = make_int4((int)(mt.A >> 31), (int)(mt.A & 0x7FFFFFFF), (int)(mt.B >> 31),
+                     (int)(mt.B & 0x7FFFFFFF));
+    e[2] = make_int4(seg_shq_global(s), 0, 0, 0);
+  };
+  for (int i = tid; i < min(send - sbeg, kSegCap); i += kThreads) seg_fill(sbeg + i, seginfo + 3 * i);
+  __syncthreads();
+  auto seg_at = [&](int sg) -> int4 {
+    return sg - sbeg < kSegCap ? seginfo[3 * (sg - sbeg)] : d.segs[sg];
+  };
+  auto seg_entry = [&](int sg, int4 &s, int4 &mat, int &shq) {
+    if (sg - sbeg < kSegCap) {
+      s = seginfo[3 * (sg - sbeg)];
+      mat = seginfo[3 * (sg - sbeg) + 1];
+      shq = seginfo[3 * (sg - sbeg) + 2].x;
+    } else {
+      int4 e[3];
+      seg_fill(sg, e);
+      s = e[0];
+      mat = e[1];
+      shq = e[2].x;
+    }
+  };
 
-    auto issue_plane = [&](int p, int issuer) {
-      tma_out |= 1u << (p & 7);
-      if (tid == issuer) {
-        const int s = p & 7;
-        mbar_expect_tx(&bars[s], kUBytes);
+  // ---- the CTA's segments as streams ---------------------------------------
+  // Segment s (column (tx, ty), owned node planes [z0, z1), z1 - z0 >= 2) has
+  // the input planes z0-1 .. z1 and the outputs z0 .. z1-1.  Inputs are
+  // numbered g over all of the CTA's segments, outputs o.  Input g goes to U
+  // slot g mod 8 (copy completion: phase g/8 mod 2 of mbarrier g mod 8) and
+  // digit slot g mod 4; output o accumulates in TMEM ring slot o mod 3, and
+  // input plane p of a segment whose first output is o_s feeds the outputs
+  // v - 1, v, v + 1 with v = o_s + p - z0.  While output o (input gin) is
+  // finished, the copies run up to input gin + 7, the digits up to the last
+  // input of output o + 2 and the MMAs (issued after the barrier) up to the
+  // last input of output o + 1, across segment boundaries.  Slots stay
+  // consistent: inputs below gin are done with (their U slots are free); the
+  // MMAs of output o's inputs are complete when o is read, so the digits in
+  // use are those of outputs o + 1 and o + 2, at most 4 inputs because every
+  // segment has two outputs or more; ring slot o + 3 = o is restarted by a
+  // bias MMA issued after the barrier that follows its read, and the zero
+  // blocks of a segment's first two inputs land on slots already read.
+  struct InCur {
+    int sg, p, z1, ob, g;  // segment, plane, its z1, its first output index; input index
+  };
+  auto in_seek = [&](InCur &c, int sg, int ob) {
+    c.sg = sg;
+    c.ob = ob;
+    if (sg < send) {
+      const int4 s = seg_at(sg);
+      c.p = s.z - 1;
+      c.z1 = s.w;
+    }
+  };
+  auto in_next = [&](InCur &c) {
+    ++c.g;
+    if (++c.p > c.z1) {
+      const int4 s = seg_at(c.sg);
+      in_seek(c, c.sg + 1, c.ob + (s.w - s.z));
+    }
+  };
+  InCur lc, dc, mc;  // copy, digit and MMA cursors
+  lc.g = dc.g = mc.g = 0;
+  in_seek(lc, sbeg, 0);
+  in_seek(dc, sbeg, 0);
+  in_seek(mc, sbeg, 0);
+  int d_shq = 0, d_xo = 0;  // digit cursor's column shift and box offset
+  if (sbeg < send) {
+    int4 s, mat;
+    seg_entry(sbeg, s, mat, d_shq);
+    d_xo = (TC_OWN * s.x - 1) & 1;
+  }
+
+  auto uslot_g = [&](int g) { return uslot + (g & 7) * (kUStride / 8); };
+  auto dslot_g = [&](int g) { return digits + (g & 3) * kDSlotBytes; };
+
+  // copies: thread kDigit0 alone issues them and keeps the cursor (the
+  // teardown reads its count from shared memory)
+  auto load_upto = [&](int gmax) {
+    if (tid != kDigit0) return;
+    while (lc.sg < send && lc.g <= gmax) {
+      {
+        const int4 s = seg_at(lc.sg);
+        const int slot = lc.g & 7;
+        mbar_expect_tx(&bars[slot], kUBytes);
         asm volatile(
             "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(uslot + s * (kUStride / 8))),
-            "l"(&tmap_u), "r"(smem_u32(&bars[s])), "r"(xbox), "r"(Y0), "r"(p), "r"(0)
+            " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(uslot_g(lc.g))),
+            "l"(&tmap_u), "r"(smem_u32(&bars[slot])), "r"((TC_OWN * s.x - 1) & ~1),
+            "r"(TC_OWN * s.y - 1), "r"(lc.p), "r"(0)
             : "memory");
       }
-    };
-    auto wait_plane = [&](int p, bool do_wait) -> bool {
-      const int s = p & 7;
-      const bool ok = do_wait ? mbar_wait(&bars[s], (uphase >> s) & 1u) : true;
-      uphase ^= 1u << s;
-      tma_out &= ~(1u << s);
-      return ok;
-    };
-    auto uslot_of = [&](int p) { return uslot + (p & 7) * (kUStride / 8); };
-    auto dslot_of = [&](int p) { return digits + (p & 3) * kDSlotBytes; };
-    // task t of a plane: node row y, component c and x parity e
-    // (t = (3 y + c) 2 + e) digitise the nine nodes x = e + 2 i, i = 0..8,
-    // once, and write the 16-byte chunks of K rows k = 3 d + c for the
-    // x-shifts d = e (nodes i = 0..7 for pairs 0..7) and d = e + 2 (nodes
-    // i = 1..8) of every stage.  With the offset-binary bias dbias =
-    // sum_s 1024 2^(11 s), digit s of q = floor(U / 2^shq) is
-    // ((q + dbias) >> 11 s) & 2047 - 1024 (q + dbias is positive and below
-    // 2^55 since |q| < 2^51); the float with bits 0x4B000000 | x is 2^23 + x,
-    // so subtracting 2^23 + 1024 leaves the digit exactly.
-    auto digitise_task = [&](int p, int t) {
-      const int e = t & 1, c = (t >> 1) % 3, y = (t >> 1) / 3;
-      const int64_t *src = uslot_of(p) + (c * kSY + y) * kSX + xo + e;
-      unsigned char *row = dslot_of(p) + y * kRowBytes;
-      unsigned char *dst0 = row + ((3 * e + c) >> 3) * 128 + ((3 * e + c) & 7) * 16;
-      unsigned char *dst1 = row + ((3 * e + 6 + c) >> 3) * 128 + ((3 * e + 6 + c) & 7) * 16;
-      uint64_t v[9];
+      in_next(lc);
+    }
+    misc[2] = (uint32_t)lc.g;
+  };
+  // task t of an input plane: node row y, component c and x parity e
+  // (t = (3 y + c) 2 + e) digitise the nine nodes x = e + 2 i, i = 0..8,
+  // once, and write the 16-byte chunks of K rows k = 3 d + c for the
+  // x-shifts d = e (nodes i = 0..7 for pairs 0..7) and d = e + 2 (nodes
+  // i = 1..8) of every stage.  With the offset-binary bias dbias =
+  // sum_s 1024 2^(11 s), digit s of q = floor(U / 2^shq) is
+  // ((q + dbias) >> 11 s) & 2047 - 1024 (q + dbias is positive and below
+  // 2^55 since |q| < 2^51); the float with bits 0x4B000000 | x is 2^23 + x,
+  // so subtracting 2^23 + 1024 leaves the digit exactly.
+  auto digitise_task = [&](int g, int xo, int shq, int t) {
+    const int e = t & 1, c = (t >> 1) % 3, y = (t >> 1) / 3;
+    const int64_t *src = uslot_g(g) + (c * kSY + y) * kSX + xo + e;
+    unsigned char *row = dslot_g(g) + y * kRowBytes;
+    unsigned char *dst0 = row + ((3 * e + c) >> 3) * 128 + ((3 * e + c) & 7) * 16;
+    unsigned char *dst1 = row + ((3 * e + 6 + c) >> 3) * 128 + ((3 * e + 6 + c) & 7) * 16;
+    uint64_t v[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) v[i] = (uint64_t)((src[2 * i] >> shq) + dbias);
+    for (int i = 0; i < 9; ++i) v[i] = (uint64_t)((src[2 * i] >> shq) + dbias);
 #pragma unroll
-      for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
-        float f[9];
+    for (int s = s_lo; s < TC_MAX_STAGES; ++s) {
+      float f[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-          f[i] = __int_as_float((int)(((uint32_t)(v[i] >> (TC_DIGIT_BITS * s)) & 2047u) |
-                                      0x4B000000u)) - 8389632.0f;
-        uint32_t w0[4], w1[4];
+      for (int i = 0; i < 9; ++i)
+        f[i] = __int_as_float((int)(((uint32_t)(v[i] >> (TC_DIGIT_BITS * s)) & 2047u) |
+                                    0x4B000000u)) - 8389632.0f;
+      uint32_t w0[4], w1[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const __half2 h0 = __floats2half2_rn(f[2 * i], f[2 * i + 1]);
-          const __half2 h1 = __floats2half2_rn(f[2 * i + 1], f[2 * i + 2]);
-          w0[i] = *reinterpret_cast<const uint32_t *>(&h0);
-          w1[i] = *reinterpret_cast<const uint32_t *>(&h1);
-        }
-        *reinterpret_cast<uint4 *>(dst0 + s * kStageBytes) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-        *reinterpret_cast<uint4 *>(dst1 + s * kStageBytes) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+      for (int i = 0; i < 4; ++i) {
+        const __half2 h0 = __floats2half2_rn(f[2 * i], f[2 * i + 1]);
+        const __half2 h1 = __floats2half2_rn(f[2 * i + 1], f[2 * i + 2]);
+        w0[i] = *reinterpret_cast<const uint32_t *>(&h0);
+        w1[i] = *reinterpret_cast<const uint32_t *>(&h1);
       }
-    };
-    // MMAs of input plane p (B variant v: 0 all outputs, 1 none below, 2 only
-    // above) into the rings of every stage, all issued by warp 8 (an issuing
-    // warp stalls while the tensor pipe drains, so no other work waits behind
-    // it).  The B start block (1 - p) mod 3 of the five stored blocks puts
-    // output z = p + o into slot z mod 3.  Input p is the first to reach
-    // output p + 1: per stage, an N = 16 MMA without accumulation first
-    // writes the magic bias 1.5 2^23 into that slot (the constant K rows of
-    // the digit block against the bias image; the epilogue read the slot's
-    // previous plane before the barrier that precedes this issue, and MMAs of
-    // one thread run in issue order).  commit: one mbarrier arrival once
-    // these and all earlier MMAs are done (batch b on mbarrier 8 + (b & 1)).
-    auto issue_mma = [&](int p, int v, int commit_batch) {
-      if (commit_batch >= 0) mma_out |= 1u << (commit_batch & 1);
-      if (warp != kMmaWarp) return;
-      __syncwarp();
-      tc_fence_after();
-      const int s0 = ((1 - p) % 3 + 3) % 3;
-      const uint32_t bimg_base = smem_u32(bimg) + (uint32_t)(v * 3 * kBImage + s0 * 256);
-      const uint32_t next_slot = (uint32_t)(16 * (((p + 1) % 3 + 3) % 3));
-      const uint64_t bias_desc = make_sdesc(smem_u32(bias_img), 256, 128);
-#pragma unroll 1
-      for (int st = s_lo; st < TC_MAX_STAGES; ++st) {
-        const uint32_t dcol = tmem_base + (uint32_t)(st * kRingCols);
-        mma_f16_elect(dcol + next_slot,
-                      make_sdesc(smem_u32(dslot_of(p) + st * kStageBytes + kRowBytes), 128, 256),
-                      bias_desc, kIdescN16, 0u);
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-          const uint32_t a = smem_u32(dslot_of(p) + st * kStageBytes + (1 + dy) * kRowBytes);
-          mma_f16_elect(dcol, make_sdesc(a, 128, 256),
-                        make_sdesc(bimg_base + (uint32_t)((dy + 1) * kBImage), kBKStride, 128),
-                        kIdescN48, 1u);
-        }
-      }
-      if (commit_batch >= 0) mma_commit_elect(&bars[8 + (commit_batch & 1)]);
-    };
-    // ---- segment prologue: TMA of planes Z0-1 .. Z0+5, digits of Z0-1 .. Z0+2,
-    // the MMAs of inputs Z0-1, Z0, Z0+1 (batch Z0+1; their bias MMAs start
-    // the slots of outputs Z0, Z0+1, Z0+2)
-    for (int p = Z0 - 1; p <= min(Z0 + 5, Z1); ++p) issue_plane(p, 0);
+      *reinterpret_cast<uint4 *>(dst0 + s * kStageBytes) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+      *reinterpret_cast<uint4 *>(dst1 + s * kStageBytes) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    }
+  };
+  // digits of the inputs up to gmax, by the threads from `first` on (they
+  // alone keep the cursor), each waiting for its input's copy
+  auto digitise_upto = [&](int gmax, int first) -> bool {
     bool ok = true;
-    for (int p = Z0 - 1; p <= min(Z0 + 2, Z1); ++p) ok = wait_plane(p, true) && ok;
-    if (sync_abort(ok)) { aborted = true; break; }
-    for (int p = Z0 - 1; p <= min(Z0 + 2, Z1); ++p)
-      for (int t = tid; t < kTasks; t += kThreads) digitise_task(p, t);
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    issue_mma(Z0 - 1, 2, -1);
-    issue_mma(Z0, 1, -1);
-    issue_mma(Z0 + 1, 0, Z0 + 1);  // Z0 + 1 <= Z1: a segment owns a plane
-
-    // the update's global operands (u^{n-1} and the multiplier C of the
-    // node) are loaded one plane ahead
-    int64_t nx_uprev[3] = {0, 0, 0}, nx_cn = 0;
-    auto load_update = [&](int L) {
-      if (MODE == TC_MODE_STEP && own && L < Z1) {
-        const int64_t n = (int64_t)L * d.plane + (int64_t)gj * d.nxp + gi;
+    if (tid < first) return ok;
+    while (dc.sg < send && dc.g <= gmax) {
+      ok = mbar_wait(&bars[dc.g & 7], (uint32_t)(dc.g >> 3) & 1u) && ok;
+      for (int t = tid - first; t < kTasks; t += kThreads - first)
+        digitise_task(dc.g, d_xo, d_shq, t);
+      const int sg = dc.sg;
+      in_next(dc);
+      if (dc.sg != sg && dc.sg < send) {
+        int4 s, mat;
+        seg_entry(dc.sg, s, mat, d_shq);
+        d_xo = (TC_OWN * s.x - 1) & 1;
+      }
+    }
+    return ok;
+  };
+  // MMAs of the inputs up to gmax into the rings of every stage, stage
+  // s_lo + r issued by the warp of rank r (a tcgen05.mma occupies its issuing
+  // warp for about a hundred cycles, so the stages are issued side by side;
+  // each stage has its own accumulators, and MMAs of one thread run in issue
+  // order).  Input plane p of a segment with first
+  // output o_s (v = o_s + p - z0) uses B variant 0 (all outputs), 1 (none
+  // below: p = z0) or 2 (only above: p = z0 - 1); the B start block
+  // (1 - v) mod 3 of the five stored blocks puts output v + k into slot
+  // (v + k) mod 3.  Input p is the first to reach output v + 1: per stage an
+  // N = 16 MMA without accumulation first writes the magic bias 1.5 2^23
+  // into that slot (the constant K rows of the digit block against the bias
+  // image).  Then each issuing warp commits onto mbarrier 8 + (batch & 1),
+  // which completes once all of them have and all their MMAs are done.  The
+  // issuing warps alone keep the cursor; there is something to issue exactly
+  // when the output the batch completes exists.
+  const int mma_rank = mma_rank_of(warp);
+  auto mma_upto = [&](int gmax, int batch) {
+    if (mma_rank < 0 || mma_rank >= STAGES || !(mc.sg < send && mc.g <= gmax)) return;
+    const int st = s_lo + mma_rank;
+    __syncwarp();
+    tc_fence_after();
+    while (mc.sg < send && mc.g <= gmax) {
+      {
+        const int z0 = seg_at(mc.sg).z;
+        const int var = mc.p == z0 - 1 ? 2 : (mc.p == z0 ? 1 : 0);
+        const int v = mc.ob + mc.p - z0;
+        const int s0 = ((1 - v) % 3 + 3) % 3;
+        const uint32_t bimg_base = smem_u32(bimg) + (uint32_t)(var * 3 * kBImage + s0 * 256);
+        const uint32_t next_slot = (uint32_t)(16 * (((v + 1) % 3 + 3) % 3));
+        const uint64_t bias_desc = make_sdesc(smem_u32(bias_img), 256, 128);
+        const unsigned char *ds = dslot_g(mc.g);
+        {
+          const uint32_t dcol = tmem_base + (uint32_t)(st * kRingCols);
+          mma_f16_elect(dcol + next_slot,
+                        make_sdesc(smem_u32(ds + st * kStageBytes + kRowBytes), 128, 256),
+                        bias_desc, kIdescN16, 0u);
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy) {
+            const uint32_t a = smem_u32(ds + st * kStageBytes + (1 + dy) * kRowBytes);
+            mma_f16_elect(dcol, make_sdesc(a, 128, 256),
+                          make_sdesc(bimg_base + (uint32_t)((dy + 1) * kBImage), kBKStride, 128),
+                          kIdescN48, 1u);
+          }
+        }
+      }
+      in_next(mc);
+    }
+    mma_commit_elect(&bars[8 + (batch & 1)]);
+  };
+  // ---- output cursor and the epilogue's view of its segment ---------------
+  int o = 0, osg = sbeg, oz = 0, oz1 = 0, gin = 1;  // output o: plane oz, input gin
+  int A1 = 0, A0 = 0, B1 = 0, B0 = 0, gi = 0, gj = 0, e_xo = 0, e_shq = 0, Rseg = 0;
+  bool own = false;
+  auto out_seek = [&](int sg) {
+    osg = sg;
+    if (sg >= send) return;
+    int4 s, mat;
+    int shq;
+    seg_entry(sg, s, mat, shq);
+    oz = s.z;
+    oz1 = s.w;
+    if (!epi) return;
+    A1 = mat.x;
+    A0 = mat.y;
+    B1 = mat.z;
+    B0 = mat.w;
+    const int X0 = TC_OWN * s.x - 1, Y0 = TC_OWN * s.y - 1;
+    e_xo = X0 & 1;  // offset of the copied box, whose x start is even
+    gi = X0 + xl;
+    gj = Y0 + yl;
+    own = epi && xl <= TC_OWN && yl <= TC_OWN && gi <= d.nx && gj <= d.ny;
+    e_shq = shq;
+    Rseg = P.eCref + P.rs - e_shq - 63;
+  };
+  // the update's global operands (u^{n-1} and the multiplier C of the node)
+  // are loaded one output ahead
+  int64_t nx_uprev[3] = {0, 0, 0}, nx_cn = 0;
+  auto load_update_at = [&](int4 s, int z) {
+    if (MODE == TC_MODE_STEP && epi) {
+      const int i = TC_OWN * s.x - 1 + xl, j = TC_OWN * s.y - 1 + yl;
+      if (xl <= TC_OWN && yl <= TC_OWN && i <= d.nx && j <= d.ny) {
+        const int64_t n = (int64_t)z * d.plane + (int64_t)j * d.nxp + i;
         nx_cn = d.C[n];
 #pragma unroll
         for (int c = 0; c < 3; ++c) nx_uprev[c] = d.U_prev[c * d.comp + n];
       }
-    };
-    load_update(Z0);
-    bool okp = true;
-    for (int L = Z0; L < Z1; ++L) {
-      // (a) this plane's update operands; the next plane's are requested
-      const int64_t nidx = (int64_t)L * d.plane + (int64_t)gj * d.nxp + gi;
-      const int64_t uprev[3] = {nx_uprev[0], nx_uprev[1], nx_uprev[2]};
-      const int64_t cn = nx_cn;
-      load_update(L + 1);
-      // plane L is complete once batch L+1 (input L+1) is in: read its slot
-      // (input L+2's bias MMA restarts it for plane L+3 after the barrier)
-      const int bL = (L + 1) & 1;
-      uint32_t w[TC_MAX_STAGES][8];
-      if (epi) {
-        __syncwarp();
-        mma_out &= ~(1u << bL);
-        const bool okm = mbar_wait(&bars[8 + bL], (mma_phase >> bL) & 1u);
-        if (!okm) atomicExch(&misc[1], 1u);
-        tc_fence_after();
-        const uint32_t tb = tmem_base + ((uint32_t)(32 * quarter) << 16) +
-                            (uint32_t)(16 * (L % 3) + 8 * jnode);
-#pragma unroll
-        for (int s = s_lo; s < TC_MAX_STAGES; ++s) tmem_ld8(tb + (uint32_t)(s * kRingCols), w[s]);
-#pragma unroll
-        for (int s = s_lo; s < TC_MAX_STAGES; ++s) tmem_wait_ld8(w[s]);
-      }
-      mma_phase ^= 1u << bL;
-      // (b) TMEM reads done, digit writes visible to the tensor core
-      tc_fence_before();
-      fence_async_smem();
-      if (sync_abort(okp)) { aborted = true; break; }
-      if (L + 2 <= Z1) issue_mma(L + 2, 0, L + 2);
+    }
+  };
+  unsigned long long or_seg = 0;
 
-      // (c) second phase: warps 9-15 digitise plane L+3 (into the digit slot
-      // of plane L-1, whose MMAs are done) and prefetch plane L+6 (into the U
-      // slot of plane L-2); warps 0-7 finish plane L.  Every thread tracks
-      // the U-slot phases.
-      okp = true;
-      if (L + 3 <= Z1) okp = wait_plane(L + 3, tid >= kDigit0);
-      if (L + 6 <= Z1) issue_plane(L + 6, kDigit0);
-      if (!epi) {  // warps 9-15: one digitisation chunk per thread (warp 8 issues MMAs)
-        if (tid >= kDigit0 && L + 3 <= Z1)
-          for (int t = tid - kDigit0; t < kTasks; t += kThreads - kDigit0) digitise_task(L + 3, t);
-        continue;
+  // ---- prologue: copies of inputs 0..7, the digits of the inputs of outputs
+  // 0 and 1 (every thread), the MMAs of output 0's inputs (batch 1)
+  if (sbeg < send) {
+    out_seek(sbeg);
+    load_upto(gin + 6);
+    const bool ok = digitise_upto(gin + (oz + 1 < oz1 ? 1 : 3) + 1, 0);
+    fence_async_smem();
+    tc_fence_before();
+    if (sync_abort(ok)) {
+      aborted = true;
+    } else {
+      mma_upto(gin + 1, 1);
+      mma_out |= 1u << 1;
+    }
+    load_update_at(seg_at(sbeg), oz);
+  }
+
+  bool okp = true;
+  while (!aborted && osg < send) {
+    // (a) this output's update operands; the next output's are requested
+    const int64_t nidx = (int64_t)oz * d.plane + (int64_t)gj * d.nxp + gi;
+    const int64_t uprev[3] = {nx_uprev[0], nx_uprev[1], nx_uprev[2]};
+    const int64_t cn = nx_cn;
+    if (MODE == TC_MODE_STEP && epi) {
+      if (oz + 1 < oz1) {
+        load_update_at(seg_at(osg), oz + 1);
+      } else if (osg + 1 < send) {
+        const int4 s = seg_at(osg + 1);
+        load_update_at(s, s.z);
       }
+    }
+    // output o is complete once batch o+1 is in: read its ring slot
+    const int bL = (o + 1) & 1;
+    uint32_t w[TC_MAX_STAGES][8];
+    if (epi) {
+      __syncwarp();
+      mma_out &= ~(1u << bL);
+      const bool okm = mbar_wait(&bars[8 + bL], (mma_phase >> bL) & 1u);
+      if (!okm) atomicExch(&misc[1], 1u);
+      tc_fence_after();
+      const uint32_t tb = tmem_base + ((uint32_t)(32 * quarter) << 16) +
+                          (uint32_t)(16 * (o % 3) + 8 * jnode);
+#pragma unroll
+      for (int s = s_lo; s < TC_MAX_STAGES; ++s) tmem_ld8(tb + (uint32_t)(s * kRingCols), w[s]);
+#pragma unroll
+      for (int s = s_lo; s < TC_MAX_STAGES; ++s) tmem_wait_ld8(w[s]);
+    }
+    mma_phase ^= 1u << bL;
+    // (b) TMEM reads done, digit writes visible to the tensor core
+    tc_fence_before();
+    fence_async_smem();
+    if (sync_abort(okp)) {
+      aborted = true;
+      break;
+    }
+    // (c) warps 8, 12-15: the MMAs of output o+1's inputs (batch o+2);
+    // thread kDigit0: copies; warps 9-12: the digits of output o+2's inputs; warps
+    // 0-7: finish output o
+    mma_upto(gin + (oz + 1 < oz1 ? 1 : 3) + 1, o + 2);
+    if (oz + 1 < oz1 || osg + 1 < send) mma_out |= 1u << ((o + 2) & 1);  // output o+1 exists
+    load_upto(gin + 7);
+    okp = digitise_upto(gin + (oz + 2 < oz1 ? 2 : 4) + 1, kDigit0);
+    if (epi) {
       // recombination (Horner over the stages), the node's own q' for the
       // 1024 q(n) term, and the material product; node columns 2 c + part
       uint64_t acc[6];
@@ -419,15 +568,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             else if (st == 3) recomb_stage<3>(a, x);
             else recomb_stage<4>(a, x);
           }
-      // plane L's slot completed its phase before the digitising warps read
-      // it; the test acquires that completion for these reads
-      if (!mbar_test_wait(&bars[L & 7], ((uphase >> (L & 7)) & 1u) ^ 1u)) atomicExch(&misc[1], 1u);
-      const int64_t *ucur = uslot_of(L);
+      // the copy of this output's plane completed before the digitising
+      // warps read it; the test acquires that completion for these reads
+      if (!mbar_test_wait(&bars[gin & 7], (uint32_t)(gin >> 3) & 1u)) atomicExch(&misc[1], 1u);
+      const int64_t *ucur = uslot_g(gin);
       int64_t u0[3], qn[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        u0[c] = ucur[(c * kSY + yl) * kSX + xl + xo];
-        const int64_t v = (u0[c] >> shq) + dbias;
+        u0[c] = ucur[(c * kSY + yl) * kSX + xl + e_xo];
+        const int64_t v = (u0[c] >> e_shq) + dbias;
         qn[c] = ((v >> lo_bits) << lo_bits) - dbias_hi;
       }
       if constexpr (MODE == TC_MODE_PARTIALS) {
@@ -449,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int c = 0; c < 3; ++c) d.S_out[c * d.comp + nidx] = S[c];
         } else if (own) {
-          // update of node (gi, gj, L): the element kernel's fixed-point step
+          // update of node (gi, gj, oz): the element kernel's fixed-point step
           const int C1 = (int)(cn >> 31), C0 = (int)(cn & 0x7FFFFFFF);
           const bool rescaled = (P.rs | P.rs_prev) != 0;
 #pragma unroll
@@ -478,23 +627,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    if (MODE == TC_MODE_STEP) {  // per-column and global bounds for the next step
-      for (int o = 16; o > 0; o >>= 1) or_seg |= __shfl_xor_sync(0xffffffffu, or_seg, o);
-      if (lane == 0 && or_seg) {
-        unsigned long long *cur = d.or_slots + (size_t)P.or_slot * (1 + d.tiles_x * d.tiles_y);
-        atomicOr(&cur[1 + seg.y * d.tiles_x + seg.x], or_seg);
-        atomicOr(&cur[0], or_seg);
+    // (d) next output; leaving a segment: its column's bounds for the next step
+    if (oz + 1 >= oz1) {
+      if (MODE == TC_MODE_STEP && epi) {
+        for (int sh = 16; sh > 0; sh >>= 1) or_seg |= __shfl_xor_sync(0xffffffffu, or_seg, sh);
+        if (lane == 0 && or_seg) {
+          const int4 s = seg_at(osg);
+          unsigned long long *cur = d.or_slots + (size_t)P.or_slot * (1 + d.tiles_x * d.tiles_y);
+          atomicOr(&cur[1 + s.y * d.tiles_x + s.x], or_seg);
+          atomicOr(&cur[0], or_seg);
+        }
       }
+      or_seg = 0;
+      out_seek(osg + 1);
+      gin += 3;
+    } else {
+      ++oz;
+      ++gin;
     }
-    __syncthreads();  // the U and digit slots are reused by the next segment
+    ++o;
   }
 
   // ---- teardown -------------------------------------------------------------
   if (aborted && tid == 0) {
     atomicOr(d.status, 1);
-    // let the copies and MMAs still in flight land (each wait bounded)
-    for (int s = 0; s < kUSlots; ++s)
-      if (tma_out & (1u << s)) mbar_wait(&bars[s], (uphase >> s) & 1u);
+    // let the copies and MMAs still in flight land (each wait bounded): the
+    // last copy into each U slot is among the last eight issued
+    const int gl = (int)misc[2];
+    for (int g = max(0, gl - kUSlots); g < gl; ++g)
+      mbar_wait(&bars[g & 7], (uint32_t)(g >> 3) & 1u);
     for (int b = 0; b < 2; ++b)
       if (mma_out & (1u << b)) mbar_wait(&bars[8 + b], (mma_phase >> b) & 1u);
   }
