@@ -35,9 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = "element·steps/s, INT8-TC vs FP64 path on 1 GB300 at ≤1e-6 rel trace error"
 UNIT = "element*steps/s"
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
-PROFILES = {"config2": os.path.join(ROOT, "profiles", "tc_step_kernel_config2_128x128x64.txt"),
-            "config3": os.path.join(ROOT, "profiles", "tc_step_kernel_config3_512x512x256.txt")}
-KERNEL_SRC = os.path.join(ROOT, "paper_2404_13683_gb300", "csrc", "vfe_tc.cu")
+PROFILES = {"config3": os.path.join(ROOT, "profiles", "tc_step_kernels_config3_512x512x256.txt")}
+# the sources of the kernels of one tensor-core step (the roofline's unit)
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2404_13683_gb300", "csrc", f)
+               for f in ("vfe_tc.cu", "vfe_stencil.cu", "vfe_tc_common.cuh")]
 
 
 def parse():
@@ -237,12 +238,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_code_hash(path=KERNEL_SRC):
-    """First 16 hex digits of the SHA-256 of the kernel source with comments
+def kernel_code_hash(paths=KERNEL_SRCS):
+    """First 16 hex digits of the SHA-256 of the kernel sources with comments
     and whitespace removed (so a comment edit keeps its profile)."""
     import re
-    with open(path) as f:
-        src = f.read()
+    src = ""
+    for path in paths:
+        with open(path) as f:
+            src += f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     src = re.sub(r"//[^\n]*", "", src)
     src = re.sub(r"\s+", "", src)
@@ -269,10 +272,15 @@ def profiled_counters(workload):
     if vals.get("kernel_code_sha256_16", "").split(" ")[0] != sha:
         return None
     try:
-        return {"dram_bytes": float(vals["dram_bytes_per_launch"]),
-                "warp_instructions": float(vals["smsp__inst_executed.sum"].split()[0])}
+        out = {"dram_bytes": float(vals["dram_bytes_per_launch"].split()[0]),
+               "warp_instructions": None}
     except (KeyError, ValueError, IndexError):
         return None
+    try:
+        out["warp_instructions"] = float(vals["smsp__inst_executed.sum"].split()[0])
+    except (KeyError, ValueError, IndexError):
+        pass
+    return out
 
 
 # warp-instruction issue rate of a GB300: 152 SMs x 4 schedulers, one warp
@@ -455,7 +463,7 @@ def run_ours(args):
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))
     roof["tensor"] = {"achieved": tc_tops, "peak": tc_peak, "unit": "TFLOP/s",
                       "frac": tc_tops / tc_peak}
-    if prof:
+    if prof and prof["warp_instructions"]:
         # the kernel is limited by instruction issue, not HBM: the same launch
         # against the GPU's warp-instruction issue rate
         ach_i = prof["warp_instructions"] / (ms_step * 1e-3)
