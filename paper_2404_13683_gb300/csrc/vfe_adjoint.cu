@@ -109,6 +109,116 @@ __global__ void __launch_bounds__(256) grad_g_kernel(int nx, int ny, int nz, con
   }
 }
 
+// The same sum on the tensor-core path, from the fixed-point states directly
+// (u = U 2^-Fu, mu = Mu 2^-Fm, padded SoA layout) and in integer arithmetic:
+// the orthogonal element's alpha = 3/4 makes 48 (16/ds) mu.(dK/dG)u an
+// integer combination of the products W_mu[i][T] W_u[j][T'] (coefficients
+// -32 and -24 for X, 48 and 36 for Y, 16, 12 and 9 for D, 48, 72 and 81 for
+// Z).  The Walsh-Hadamard sums are exact in int64 on U >> 3 (|U| < 2^62);
+// each state's 24 coefficients of the element are then cut to 31 bits below
+// the largest of them (W >> s, one s per element and state), the 57 products
+// of two such are split at bit 31 and the halves summed separately, so
+// nothing overflows (57 x 81 x 2^31 < 2^44), and one FP64 conversion per
+// element and step carries the result, 2^(6 + s_u + s_mu) 2^-(Fu + Fm) ds /
+// (16 48) dt^2, into the gradient.  The cut costs at most 2^-30 of the
+// element's largest coefficient, far below the accuracy the states carry.
+__device__ __forceinline__ void wht8_i64(int64_t *v) {
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      if (!((a >> m) & 1)) {
+        const int64_t lo = v[a], hi = v[a | (1 << m)];
+        v[a] = hi + lo;
+        v[a | (1 << m)] = hi - lo;
+      }
+}
+
+__global__ void __launch_bounds__(256) grad_g_tc_kernel(int nx, int ny, int nz, const int32_t *mat,
+                                                        const int64_t *Uf, const int64_t *Fu,
+                                                        const int64_t *Mu, const int64_t *Fm,
+                                                        int nxp, int64_t plane, int64_t comp,
+                                                        double scale, double *grad) {
+  const int64_t ne = (int64_t)nx * ny * nz;
+  const int fexp = 6 - (int)(*Fu) - (int)(*Fm);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (mat[e] < 0) continue;
+    const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+    int64_t wm[3][8], wu[3][8];
+    uint64_t om = 0, ou = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int64_t t = c * comp + (ez + (a >> 2)) * plane + (ey + ((a >> 1) & 1)) * nxp +
+                          (ex + (a & 1));
+        wm[c][a] = Mu[t] >> 3;
+        wu[c][a] = Uf[t] >> 3;
+      }
+      wht8_i64(wm[c]);
+      wht8_i64(wu[c]);
+#pragma unroll
+      for (int T = 0; T < 8; ++T) {
+        om |= (uint64_t)(wm[c][T] ^ (wm[c][T] >> 63));
+        ou |= (uint64_t)(wu[c][T] ^ (wu[c][T] >> 63));
+      }
+    }
+    // |W| < 2^b: keep 31 bits below the top (W >> s lies in [-2^31, 2^31))
+    const int sm = max(0, (64 - __clzll((long long)om)) - 31);
+    const int su = max(0, (64 - __clzll((long long)ou)) - 31);
+    int M[3][8], U[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int T = 0; T < 8; ++T) {
+        M[c][T] = (int)(wm[c][T] >> sm);
+        U[c][T] = (int)(wu[c][T] >> su);
+      }
+    int64_t hi = 0, lo = 0;
+    auto term = [&](int coef, int a, int b) {
+      const int64_t p = (int64_t)a * (int64_t)b;
+      hi += (int64_t)coef * (p >> 31);
+      lo += (int64_t)coef * (p & 0x7FFFFFFF);
+    };
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int bi = 1 << i;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (j == i) continue;
+        const int bj = 1 << j, bp = 7 ^ bi ^ bj;
+        term(-32, M[i][bi], U[j][bj]);             // X
+        term(-24, M[i][bi | bp], U[j][bj | bp]);
+        term(48, M[i][bj], U[j][bi]);              // Y
+        term(36, M[i][bj | bp], U[j][bi | bp]);
+      }
+      const int bm = 1 << ((i + 1) % 3), bn = 1 << ((i + 2) % 3);
+      term(16, M[i][bi], U[i][bi]);                // D
+      term(12, M[i][bi | bm], U[i][bi | bm]);
+      term(12, M[i][bi | bn], U[i][bi | bn]);
+      term(9, M[i][7], U[i][7]);
+#pragma unroll
+      for (int T = 1; T < 8; ++T) {                // Z
+        const int n = (T & 1) + ((T >> 1) & 1) + ((T >> 2) & 1);
+        term(n == 1 ? 48 : (n == 2 ? 72 : 81), M[i][T], U[i][T]);
+      }
+    }
+    grad[e] += ldexp(scale * ((double)hi * 2147483648.0 + (double)lo), fexp + sm + su);
+  }
+}
+
+cudaError_t grad_g_tc_accumulate(cudaStream_t s, int nx, int ny, int nz, const int32_t *mat,
+                                 double ds, const int64_t *Uf, const int64_t *Fu,
+                                 const int64_t *Mu, const int64_t *Fm, int nxp, int64_t plane,
+                                 int64_t comp, double scale, double *grad) {
+  const int64_t ne = (int64_t)nx * ny * nz;
+  const int blocks = (int)((ne + 255) / 256 < 8192 ? (ne + 255) / 256 : 8192);
+  grad_g_tc_kernel<<<blocks, 256, 0, s>>>(nx, ny, nz, mat, Uf, Fu, Mu, Fm, nxp, plane, comp,
+                                          scale * ds / (16.0 * 48.0), grad);
+  return cudaGetLastError();
+}
+
 cudaError_t tc_state_to_f64(cudaStream_t s, const int64_t *U, const int64_t *persist,
                             int extra_shift, int nx, int ny, int64_t nn, int nxp, int64_t plane,
                             int64_t comp, double *out) {

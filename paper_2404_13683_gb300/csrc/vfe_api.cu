@@ -2377,6 +2377,11 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
   vfe_mesh *adj = nullptr;
   std::vector<Snapshot> snaps(nb);
   double *d_block = nullptr, *d_mu = nullptr, *d_grad = nullptr;
+  // tensor-core path: the recomputed forward states stay in fixed point, with
+  // the exponent of each step
+  void *d_ublock = nullptr;
+  int64_t *d_uexp = nullptr;
+  const bool tc = m->opt.path == VFE_PATH_TC;
   int rc = VFE_OK;
   do {
     // the adjoint runs on a twin mesh: same geometry, materials, dt and path,
@@ -2420,13 +2425,30 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
     // dK_e/dG at fixed kappa comes from the element's closed form (alpha)
     const double alpha = m->opt.element_kind == VFE_OVFEM ? 0.75 : 1.0 / 3.0;
     const size_t fb = sizeof(double) * 3 * m->nn;
+    const size_t sb = state_bytes(m);
     cudaError_t e;
-    if ((e = cudaMalloc(&d_block, fb * (C + 1))) != cudaSuccess ||
-        (e = cudaMalloc(&d_mu, fb)) != cudaSuccess ||
+    if (tc && (adj->nxp != m->nxp || adj->plane != m->plane || adj->comp != m->comp)) {
+      rc = fail(VFE_EINVAL, "internal: adjoint twin has another state layout");
+      break;
+    }
+    if ((tc ? ((e = cudaMalloc(&d_ublock, sb * (C + 1))) != cudaSuccess ||
+               (e = cudaMalloc((void **)&d_uexp, sizeof(int64_t) * (C + 1))) != cudaSuccess)
+            : ((e = cudaMalloc(&d_block, fb * (C + 1))) != cudaSuccess ||
+               (e = cudaMalloc(&d_mu, fb)) != cudaSuccess)) ||
         (e = cudaMalloc(&d_grad, sizeof(double) * m->ne)) != cudaSuccess) {
       rc = fail(VFE_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(e));
       break;
     }
+    // u^n of the forward run into block slot j (fixed point and its exponent
+    // on the tensor-core path, FP64 otherwise)
+    auto keep_state = [&](int j) -> int {
+      if (!tc) return state_to_f64(m, d_block + (size_t)j * 3 * m->nn);
+      CUDA_TRY(cudaMemcpyAsync((char *)d_ublock + sb * j, m->d_U[m->cur], sb,
+                               cudaMemcpyDeviceToDevice, m->stream));
+      CUDA_TRY(cudaMemcpyAsync(d_uexp + j, m->d_tcpersist, sizeof(int64_t),
+                               cudaMemcpyDeviceToDevice, m->stream));
+      return VFE_OK;
+    };
     if ((e = cudaMemset(d_grad, 0, sizeof(double) * m->ne)) != cudaSuccess) {
       rc = fail(VFE_ECUDA, "gradient buffer: %s", cudaGetErrorString(e));
       break;
@@ -2435,17 +2457,26 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
     for (int b = nb - 1; b >= 0 && rc == VFE_OK; --b) {
       const int s0 = b * C, len = std::min(C, N - s0);
       if ((rc = snap_restore(m, snaps[b])) != VFE_OK) break;
-      if ((rc = state_to_f64(m, d_block)) != VFE_OK) break;
+      if ((rc = keep_state(0)) != VFE_OK) break;
       for (int j = 1; j <= len && rc == VFE_OK; ++j) {
         if ((rc = vfe_step(m, 1)) != VFE_OK) break;
-        rc = state_to_f64(m, d_block + (size_t)j * 3 * m->nn);
+        rc = keep_state(j);
       }
       for (int mi = s0 + len; mi >= s0 + 1 && rc == VFE_OK; --mi) {
         if ((rc = vfe_step(adj, 1)) != VFE_OK) break;  // mu^{mi-1}
-        if ((rc = state_to_f64(adj, d_mu)) != VFE_OK) break;
-        const cudaError_t ge = grad_g_accumulate(
-            m->stream, m->nx, m->ny, m->nz, m->d_mat, alpha, m->h,
-            d_block + (size_t)(mi - 1 - s0) * 3 * m->nn, d_mu, m->dt * m->dt, d_grad);
+        const int j = mi - 1 - s0;
+        cudaError_t ge;
+        if (tc) {
+          // straight from the two fixed-point states (same stream)
+          ge = grad_g_tc_accumulate(m->stream, m->nx, m->ny, m->nz, m->d_mat, m->h,
+                                    (const int64_t *)((char *)d_ublock + sb * j), d_uexp + j,
+                                    adj->d_U[adj->cur], adj->d_tcpersist, m->nxp, m->plane,
+                                    m->comp, m->dt * m->dt, d_grad);
+        } else {
+          if ((rc = state_to_f64(adj, d_mu)) != VFE_OK) break;
+          ge = grad_g_accumulate(m->stream, m->nx, m->ny, m->nz, m->d_mat, alpha, m->h,
+                                 d_block + (size_t)j * 3 * m->nn, d_mu, m->dt * m->dt, d_grad);
+        }
         if (ge != cudaSuccess) rc = fail(VFE_ECUDA, "gradient kernel: %s", cudaGetErrorString(ge));
       }
     }
@@ -2462,6 +2493,8 @@ int vfe_misfit_gradient(vfe_mesh *m, int nsteps, const double *data, int checkpo
   for (auto &s : snaps) snap_free(s);
   if (d_block) cudaFree(d_block);
   if (d_mu) cudaFree(d_mu);
+  if (d_ublock) cudaFree(d_ublock);
+  if (d_uexp) cudaFree(d_uexp);
   if (d_grad) cudaFree(d_grad);
   if (adj) vfe_destroy(adj);
   g_last_error = msg;

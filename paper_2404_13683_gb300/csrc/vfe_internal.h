@@ -236,6 +236,12 @@ cudaError_t tc_state_to_f64(cudaStream_t s, const int64_t *U, const int64_t *per
 cudaError_t grad_g_accumulate(cudaStream_t s, int nx, int ny, int nz, const int32_t *mat,
                               double alpha, double ds, const double *u, const double *mu,
                               double scale, double *grad);
+// the same on the tensor-core path from the fixed-point states (forward U with
+// its exponent *Fu, adjoint Mu with *Fm; padded SoA layout)
+cudaError_t grad_g_tc_accumulate(cudaStream_t s, int nx, int ny, int nz, const int32_t *mat,
+                                 double ds, const int64_t *Uf, const int64_t *Fu,
+                                 const int64_t *Mu, const int64_t *Fm, int nxp, int64_t plane,
+                                 int64_t comp, double scale, double *grad);
 
 size_t f64_params_bytes();
 cudaError_t f64_launch_prologue(cudaStream_t s, void *params, int64_t *persist,
