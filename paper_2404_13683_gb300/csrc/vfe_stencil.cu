@@ -44,9 +44,9 @@
 // to seven planes ahead, and the digits and MMAs of the next segment's first
 // planes are made while the current one finishes, so a segment boundary
 // costs no pipeline refill.  Per output plane the 8 epilogue warps read its
-// TMEM slot, recombine and update the node plane while warps 8 and 12-15
-// issue the MMAs of the next output's inputs (one digit stage each) and
-// warps 9-12 digitise the inputs of the
+// TMEM slot, recombine and update the node plane while warps 8 and 13-15
+// issue the MMAs of the next output's inputs (the digit stages shared out)
+// and warps 9-12 digitise the inputs of the
 // output after it (one CTA barrier per output plane).  Source and receiver
 // planes, mesh faces and material interfaces are left to the element kernel
 // (vfe_tc.cu).
@@ -108,12 +108,17 @@ constexpr int kTmemCols = 256;
 constexpr int kRingCols = 48;                 // one stage: slots of planes z mod 3
 constexpr int kTasks = kSY * 3 * 2;           // digitisation tasks per plane
 constexpr int kEpiWarps = 8;                  // warps 0-7: epilogue (lane quarter x node)
-// MMA issue: one warp per digit stage, warps 8, 12, 13, 14, 15 (warps 12-15
-// have no or few digitisation tasks); stage s_lo + r from the warp of rank r
+// MMA issue: warps 8, 13, 14, 15 (ranks 0-3), stage s_lo + k from the warp
+// of rank k mod 4; digitisation: warps 9-12, 27 tasks each (one warp per
+// scheduler, none of them issuing MMAs)
+constexpr int kMmaWarps = 4;
 __device__ __forceinline__ int mma_rank_of(int warp) {
-  return warp == 8 ? 0 : (warp >= 12 ? warp - 11 : -1);
+  return warp == 8 ? 0 : (warp >= 13 ? warp - 12 : -1);
 }
-constexpr int kDigit0 = 9 * 32;               // first digitising thread (warps 9-15)
+constexpr int kDigit0 = 9 * 32;               // first digitising thread (warps 9-12)
+constexpr int kDigitWarps = 4;
+constexpr int kTasksPerWarp = 27;
+static_assert(kDigitWarps * kTasksPerWarp == 18 * 3 * 2, "digitisation tasks per plane");
 static_assert(kThreads - kDigit0 >= kTasks, "one task per digitising thread");
 
 // kind::f16, D f32, A f16 MN-major, B f16 K-major, N = 48, M = 128
@@ -163,8 +168,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     misc[1] = 0;
     misc[2] = 0;
     for (int i = 0; i < kUSlots; ++i) mbar_init(&bars[i], 1);
-    mbar_init(&bars[8], STAGES);  // one commit per issuing warp
-    mbar_init(&bars[9], STAGES);
+    mbar_init(&bars[8], STAGES < kMmaWarps ? STAGES : kMmaWarps);  // one commit per issuing warp
+    mbar_init(&bars[9], STAGES < kMmaWarps ? STAGES : kMmaWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -381,13 +386,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
   // digits of the inputs up to gmax, by the threads from `first` on (they
   // alone keep the cursor), each waiting for its input's copy
+  // (first = 0: every thread, tasks strided over the block; first = kDigit0:
+  // warps 9-12, kTasksPerWarp tasks each)
   auto digitise_upto = [&](int gmax, int first) -> bool {
     bool ok = true;
-    if (tid < first) return ok;
+    if (tid < first || (first > 0 && tid >= kDigit0 + 32 * kDigitWarps)) return ok;
+    const int t_own = first > 0 ? (lane < kTasksPerWarp ? (warp - 9) * kTasksPerWarp + lane : -1)
+                                : -1;
     while (dc.sg < send && dc.g <= gmax) {
       ok = mbar_wait(&bars[dc.g & 7], (uint32_t)(dc.g >> 3) & 1u) && ok;
-      for (int t = tid - first; t < kTasks; t += kThreads - first)
-        digitise_task(dc.g, d_xo, d_shq, t);
+      if (first > 0) {
+        if (t_own >= 0) digitise_task(dc.g, d_xo, d_shq, t_own);
+      } else {
+        for (int t = tid; t < kTasks; t += kThreads) digitise_task(dc.g, d_xo, d_shq, t);
+      }
       const int sg = dc.sg;
       in_next(dc);
       if (dc.sg != sg && dc.sg < send) {
@@ -399,10 +411,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     return ok;
   };
   // MMAs of the inputs up to gmax into the rings of every stage, stage
-  // s_lo + r issued by the warp of rank r (a tcgen05.mma occupies its issuing
-  // warp for about a hundred cycles, so the stages are issued side by side;
-  // each stage has its own accumulators, and MMAs of one thread run in issue
-  // order).  Input plane p of a segment with first
+  // s_lo + k issued by the warp of rank k mod 4 (a tcgen05.mma occupies its
+  // issuing warp for about a hundred cycles, so the stages are issued side by
+  // side; each stage has its own accumulators, and MMAs of one thread run in
+  // issue order).  Input plane p of a segment with first
   // output o_s (v = o_s + p - z0) uses B variant 0 (all outputs), 1 (none
   // below: p = z0) or 2 (only above: p = z0 - 1); the B start block
   // (1 - v) mod 3 of the five stored blocks puts output v + k into slot
@@ -416,7 +428,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int mma_rank = mma_rank_of(warp);
   auto mma_upto = [&](int gmax, int batch) {
     if (mma_rank < 0 || mma_rank >= STAGES || !(mc.sg < send && mc.g <= gmax)) return;
-    const int st = s_lo + mma_rank;
     __syncwarp();
     tc_fence_after();
     while (mc.sg < send && mc.g <= gmax) {
@@ -429,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t next_slot = (uint32_t)(16 * (((v + 1) % 3 + 3) % 3));
         const uint64_t bias_desc = make_sdesc(smem_u32(bias_img), 256, 128);
         const unsigned char *ds = dslot_g(mc.g);
-        {
+        for (int st = s_lo + mma_rank; st < TC_MAX_STAGES; st += kMmaWarps) {
           const uint32_t dcol = tmem_base + (uint32_t)(st * kRingCols);
           mma_f16_elect(dcol + next_slot,
                         make_sdesc(smem_u32(ds + st * kStageBytes + kRowBytes), 128, 256),
@@ -543,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       aborted = true;
       break;
     }
-    // (c) warps 8, 12-15: the MMAs of output o+1's inputs (batch o+2);
+    // (c) warps 8, 13-15: the MMAs of output o+1's inputs (batch o+2);
     // thread kDigit0: copies; warps 9-12: the digits of output o+2's inputs; warps
     // 0-7: finish output o
     mma_upto(gin + (oz + 1 < oz1 ? 1 : 3) + 1, o + 2);
