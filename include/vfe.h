@@ -308,9 +308,12 @@ int vfe_set_shear_moduli(vfe_mesh *mesh, const double *G);
  * vfe_create_batch takes n distinct meshes on the tensor-core path, on one
  * device; it keeps pointers to them (they must outlive the batch).  Meshes
  * may differ in their digit stage count.  vfe_batch_step(b, n) advances every
- * mesh n steps with one fused kernel launch per step and stage count over
- * those meshes' node columns (plus one per-step prologue launch), replayed as
- * captured CUDA graphs of 32 and of 2 steps; each mesh
+ * mesh n steps: per step one prologue launch, one fused element-kernel launch
+ * per stage count over those meshes' non-uniform node columns (all of a
+ * mesh's columns when its stencil option is off), and for each mesh with
+ * the node-stencil kernel one stencil launch over its uniform runs on a
+ * share of the SMs in proportion to its size, on side streams that run side
+ * by side; replayed as captured CUDA graphs of 32 and of 2 steps; each mesh
  * keeps its own source, receivers, traces, state and time step.  Work queued
  * on a mesh's own stream before the call runs first; calls on a mesh after it
  * wait for the batch.  Changing a mesh's source or receivers between batch

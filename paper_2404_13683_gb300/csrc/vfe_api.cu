@@ -193,6 +193,10 @@ struct vfe_mesh {
   // node-stencil kernel on the uniform runs (stencil_on): its segments, their
   // material, its CTA ranges, its B image and its tensor maps (box 20x18x1x3)
   bool stencil_on = false;
+  // the runs before their split over the CTAs (a batch splits them again):
+  // element-kernel runs, stencil runs and their materials
+  std::vector<int4> el_runs, st_runs;
+  std::vector<int32_t> st_rmat;
   std::vector<int4> st_segs;
   std::vector<int32_t> st_mat, st_off;
   int st_ctas = 0;
@@ -779,9 +783,15 @@ static int build_segments(vfe_mesh *m) {
   if (m->stencil_on) {
     split_runs(el_runs, nullptr, ctas, 2.0, m->segs, nullptr, m->seg_off);
     split_runs(st_runs, &st_rmat, ctas, 0.0, m->st_segs, &m->st_mat, m->st_off, 2);
+    m->el_runs = el_runs;
+    m->st_runs = st_runs;
+    m->st_rmat = st_rmat;
   } else {
     m->segs = all_segs;
     m->seg_off = all_off;
+    m->el_runs.clear();
+    m->st_runs.clear();
+    m->st_rmat.clear();
     m->st_segs.clear();
     m->st_mat.clear();
     m->st_off.assign(1, 0);
@@ -1922,6 +1932,19 @@ struct vfe_batch {
   TcDevice *d_devs[2] = {nullptr, nullptr};
   CUtensorMap *d_maps[2] = {nullptr, nullptr};
   TcPrologueArgs *d_pro = nullptr;
+  // meshes with the node-stencil kernel: their uniform runs go to one stencil
+  // launch per mesh, split over a share of the SMs in proportion to the
+  // mesh's planes, on side streams that run side by side with the batched
+  // element kernel (the two touch disjoint nodes of each mesh)
+  struct StencilPart {
+    int mesh, n_ctas;
+    int4 *d_segs;
+    int32_t *d_off, *d_mat;
+  };
+  std::vector<StencilPart> st_parts;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_done;
+  cudaEvent_t fork = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};       // two steps from parity p
   cudaGraphExec_t graph_long[2] = {nullptr, nullptr};  // kLongSteps steps
 };
@@ -1931,6 +1954,12 @@ static void batch_free_arrays(vfe_batch *b) {
                   b->d_devs[0], b->d_devs[1], b->d_maps[0], b->d_maps[1], b->d_pro};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  for (vfe_batch::StencilPart &q : b->st_parts) {
+    if (q.d_segs) cudaFree(q.d_segs);
+    if (q.d_off) cudaFree(q.d_off);
+    if (q.d_mat) cudaFree(q.d_mat);
+  }
+  b->st_parts.clear();
   b->d_segs = nullptr; b->d_seg_mesh = nullptr; b->d_seg_off = nullptr; b->d_recv_off = nullptr;
   b->d_recv = nullptr; b->d_devs[0] = b->d_devs[1] = nullptr; b->d_maps[0] = b->d_maps[1] = nullptr;
   b->d_pro = nullptr;
@@ -1950,42 +1979,68 @@ static int batch_build(vfe_batch *b) {
   b->seg_mesh.clear();
   b->seg_off.clear();
   b->groups.clear();
-  // per stage count (ascending), the column-planes of its meshes in order,
-  // split into one equal range per SM
+  // per stage count (ascending), the element-kernel runs of its meshes (all
+  // of a mesh's column-planes when it has no stencil kernel), split over the
+  // SMs in the element kernel's cost model
   for (int st = 1; st <= TC_MAX_STAGES; ++st) {
-    std::vector<int> idx;
-    for (int i = 0; i < nm; ++i)
-      if (b->meshes[i]->opt.stages == st) idx.push_back(i);
-    if (idx.empty()) continue;
-    std::vector<int64_t> start(idx.size() + 1, 0);
-    for (size_t q = 0; q < idx.size(); ++q) {
-      const vfe_mesh *m = b->meshes[idx[q]];
-      start[q + 1] = start[q] + (int64_t)m->tiles_x * m->tiles_y * (m->nz + 1);
-    }
-    const int64_t total = start.back();
-    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(b->sms, total));
-    vfe_batch::Group grp;
-    grp.stages = st;
-    grp.n_ctas = (int)G;
-    grp.off_base = (int)b->seg_off.size();
-    for (int64_t g = 0; g < G; ++g) {
-      b->seg_off.push_back((int32_t)b->segs.size());
-      int64_t lo = g * total / G;
-      const int64_t hi = (g + 1) * total / G;
-      while (lo < hi) {
-        const int q = (int)(std::upper_bound(start.begin(), start.end(), lo) - start.begin()) - 1;
-        const vfe_mesh *m = b->meshes[idx[q]];
-        const int64_t planes = m->nz + 1, loc = lo - start[q];
-        const int64_t col = loc / planes, z0 = loc % planes;
-        const int64_t z1 = std::min<int64_t>(planes, z0 + std::min(hi, start[q + 1]) - lo);
-        b->segs.push_back(make_int4((int)(col % m->tiles_x), (int)(col / m->tiles_x), (int)z0,
-                                    (int)z1));
-        b->seg_mesh.push_back(idx[q]);
-        lo += z1 - z0;
+    std::vector<int4> runs;
+    std::vector<int32_t> run_mesh;
+    for (int i = 0; i < nm; ++i) {
+      const vfe_mesh *m = b->meshes[i];
+      if (m->opt.stages != st) continue;
+      if (m->stencil_on) {
+        runs.insert(runs.end(), m->el_runs.begin(), m->el_runs.end());
+        run_mesh.insert(run_mesh.end(), m->el_runs.size(), i);
+      } else {
+        for (int ty = 0; ty < m->tiles_y; ++ty)
+          for (int tx = 0; tx < m->tiles_x; ++tx) {
+            runs.push_back(make_int4(tx, ty, 0, m->nz + 1));
+            run_mesh.push_back(i);
+          }
       }
     }
-    b->seg_off.push_back((int32_t)b->segs.size());
+    if (runs.empty()) continue;
+    std::vector<int4> gsegs;
+    std::vector<int32_t> gmesh, goff;
+    split_runs(runs, &run_mesh, b->sms, 2.0, gsegs, &gmesh, goff);
+    vfe_batch::Group grp;
+    grp.stages = st;
+    grp.n_ctas = (int)goff.size() - 1;
+    grp.off_base = (int)b->seg_off.size();
+    const int32_t base = (int32_t)b->segs.size();
+    for (int32_t o : goff) b->seg_off.push_back(base + o);
+    b->segs.insert(b->segs.end(), gsegs.begin(), gsegs.end());
+    b->seg_mesh.insert(b->seg_mesh.end(), gmesh.begin(), gmesh.end());
     b->groups.push_back(grp);
+  }
+  // the stencil parts: each mesh's uniform runs over its share of the SMs
+  {
+    int64_t all = 0;
+    for (int i = 0; i < nm; ++i)
+      for (const int4 &r : b->meshes[i]->st_runs) all += r.w - r.z;
+    for (int i = 0; i < nm && all > 0; ++i) {
+      vfe_mesh *m = b->meshes[i];
+      if (!m->stencil_on || m->st_runs.empty()) continue;
+      int64_t planes = 0;
+      for (const int4 &r : m->st_runs) planes += r.w - r.z;
+      const int ctas = (int)std::max<int64_t>(
+          1, std::min<int64_t>(b->sms, (planes * b->sms + all / 2) / all));
+      std::vector<int4> psegs;
+      std::vector<int32_t> pmat, poff;
+      split_runs(m->st_runs, &m->st_rmat, ctas, 0.0, psegs, &pmat, poff, 2);
+      vfe_batch::StencilPart q;
+      q.mesh = i;
+      q.n_ctas = (int)poff.size() - 1;
+      q.d_segs = nullptr;
+      q.d_off = nullptr;
+      q.d_mat = nullptr;
+      b->st_parts.push_back(q);
+      vfe_batch::StencilPart &qq = b->st_parts.back();
+      int rc;
+      if ((rc = upload_vec(&qq.d_segs, psegs)) != VFE_OK) return rc;
+      if ((rc = upload_vec(&qq.d_off, poff)) != VFE_OK) return rc;
+      if ((rc = upload_vec(&qq.d_mat, pmat)) != VFE_OK) return rc;
+    }
   }
   // receivers per batch segment (indices into each mesh's own trace rows)
   const int ns = (int)b->segs.size();
@@ -2093,8 +2148,29 @@ static TcBatch batch_args(const vfe_batch *b, int parity, const vfe_batch::Group
 // meshes with the same digit stage count
 static int batch_enqueue(vfe_batch *b, int parity) {
   CUDA_TRY(tc_launch_batch_prologue(b->stream, b->d_pro, (int)b->meshes.size()));
+  const int ns = (int)b->side.size();
+  if (!b->st_parts.empty()) {
+    CUDA_TRY(cudaEventRecord(b->fork, b->stream));
+    for (int k = 0; k < ns; ++k) CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->fork, 0));
+    for (size_t k = 0; k < b->st_parts.size(); ++k) {
+      const vfe_batch::StencilPart &q = b->st_parts[k];
+      vfe_mesh *m = b->meshes[q.mesh];
+      const int cur = b->base_cur[q.mesh] ^ parity;
+      TcDevice d = tc_stencil_device(m, cur);
+      d.segs = q.d_segs;
+      d.seg_off = q.d_off;
+      d.seg_mat = q.d_mat;
+      d.n_ctas = q.n_ctas;
+      CUDA_TRY(stencil_launch_ex(b->side[k % ns], d, &m->st_tmap[cur], TC_MODE_STEP, false));
+    }
+  }
   for (const vfe_batch::Group &g : b->groups)
-    CUDA_TRY(tc_launch_batch_step(b->stream, batch_args(b, parity, g), g.stages));
+    if (g.n_ctas > 0) CUDA_TRY(tc_launch_batch_step(b->stream, batch_args(b, parity, g), g.stages));
+  if (!b->st_parts.empty())
+    for (int k = 0; k < ns; ++k) {
+      CUDA_TRY(cudaEventRecord(b->side_done[k], b->side[k]));
+      CUDA_TRY(cudaStreamWaitEvent(b->stream, b->side_done[k], 0));
+    }
   return VFE_OK;
 }
 
@@ -2122,8 +2198,19 @@ int vfe_create_batch(int n, vfe_mesh *const *meshes, vfe_batch **out) {
   b->sms = meshes[0]->sms;
   int rc = VFE_OK;
   cudaSetDevice(b->device);
-  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+  bool ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  const int nside = std::min(n, 128);  // one side stream per mesh: the stencil launches run side by side
+  for (int k = 0; k < nside && ok; ++k) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e = nullptr;
+    ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->side.push_back(s);
+    ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (ok) b->side_done.push_back(e);
+  }
+  if (!ok) {
     rc = fail(VFE_ECUDA, "batch stream/event creation failed");
   } else {
     for (vfe_mesh *m : b->meshes)
@@ -2144,8 +2231,12 @@ int vfe_destroy_batch(vfe_batch *b) {
   if (!b) return VFE_OK;
   cudaSetDevice(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
+  for (cudaStream_t s : b->side) cudaStreamSynchronize(s);
   batch_free_arrays(b);
   if (b->done) cudaEventDestroy(b->done);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->side_done) cudaEventDestroy(e);
+  for (cudaStream_t s : b->side) cudaStreamDestroy(s);
   if (b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return VFE_OK;

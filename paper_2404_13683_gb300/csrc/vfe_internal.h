@@ -228,6 +228,8 @@ cudaError_t stencil_prepare();
 // the node-stencil kernel over d.segs / d.seg_off / d.seg_mat (d.n_ctas CTAs;
 // nothing is launched for 0); tmap: box ST_BOXX x ST_BOXY x 1 x 3
 cudaError_t stencil_launch(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
+cudaError_t stencil_launch_ex(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode,
+                              bool pdl);
 
 cudaError_t tc_state_to_f64(cudaStream_t s, const int64_t *U, const int64_t *persist,
                             int extra_shift, int nx, int ny, int64_t nn, int nxp, int64_t plane,

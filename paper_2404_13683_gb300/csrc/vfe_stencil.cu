@@ -704,7 +704,7 @@ cudaError_t stencil_prepare() {
 
 template <int MODE, int S>
 static cudaError_t st_launch_one(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap,
-                                 int n_ctas) {
+                                 int n_ctas, bool pdl) {
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3(n_ctas);
@@ -715,28 +715,35 @@ static cudaError_t st_launch_one(cudaStream_t s, const TcDevice &d, const CUtens
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = MODE == TC_MODE_STEP ? 1 : 0;
+  cfg.numAttrs = MODE == TC_MODE_STEP && pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, tc_stencil_kernel<MODE, S>, *tmap, d);
 }
 
 template <int MODE>
 static cudaError_t st_launch_mode(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap,
-                                  int stages, int n_ctas) {
+                                  int stages, int n_ctas, bool pdl) {
   switch (stages) {
-    case 1: return st_launch_one<MODE, 1>(s, d, tmap, n_ctas);
-    case 2: return st_launch_one<MODE, 2>(s, d, tmap, n_ctas);
-    case 3: return st_launch_one<MODE, 3>(s, d, tmap, n_ctas);
-    case 4: return st_launch_one<MODE, 4>(s, d, tmap, n_ctas);
-    default: return st_launch_one<MODE, 5>(s, d, tmap, n_ctas);
+    case 1: return st_launch_one<MODE, 1>(s, d, tmap, n_ctas, pdl);
+    case 2: return st_launch_one<MODE, 2>(s, d, tmap, n_ctas, pdl);
+    case 3: return st_launch_one<MODE, 3>(s, d, tmap, n_ctas, pdl);
+    case 4: return st_launch_one<MODE, 4>(s, d, tmap, n_ctas, pdl);
+    default: return st_launch_one<MODE, 5>(s, d, tmap, n_ctas, pdl);
   }
 }
 
-// d.segs / d.seg_off / d.seg_mat / d.n_ctas describe the stencil segments
-cudaError_t stencil_launch(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode) {
+// d.segs / d.seg_off / d.seg_mat / d.n_ctas describe the stencil segments;
+// pdl: a time step is launched as a programmatic dependent of the kernel
+// before it on the stream
+cudaError_t stencil_launch_ex(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode,
+                              bool pdl) {
   if (d.n_ctas <= 0) return cudaSuccess;
   switch (mode) {
-    case TC_MODE_STEP: return st_launch_mode<TC_MODE_STEP>(s, d, tmap, d.stages, d.n_ctas);
-    case TC_MODE_KU: return st_launch_mode<TC_MODE_KU>(s, d, tmap, d.stages, d.n_ctas);
-    default: return st_launch_mode<TC_MODE_PARTIALS>(s, d, tmap, d.stages, d.n_ctas);
+    case TC_MODE_STEP: return st_launch_mode<TC_MODE_STEP>(s, d, tmap, d.stages, d.n_ctas, pdl);
+    case TC_MODE_KU: return st_launch_mode<TC_MODE_KU>(s, d, tmap, d.stages, d.n_ctas, pdl);
+    default: return st_launch_mode<TC_MODE_PARTIALS>(s, d, tmap, d.stages, d.n_ctas, pdl);
   }
+}
+
+cudaError_t stencil_launch(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode) {
+  return stencil_launch_ex(s, d, tmap, mode, true);
 }

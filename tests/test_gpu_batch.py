@@ -1,5 +1,7 @@
-"""Batched stepping of several meshes in one launch per step (the many-case
-use): bit-identical to stepping each mesh alone, and against the oracle."""
+"""Batched stepping of several meshes (the many-case use): one fused element
+kernel launch per step and stage count, plus each mesh's node-stencil launch
+on side streams; bit-identical to stepping each mesh alone, and against the
+oracle."""
 import numpy as np
 import pytest
 
@@ -21,8 +23,8 @@ def test_batch_equals_individual_runs():
     models = _models()
     nsteps = 23
     alone = []
-    for w in models:   # the element kernel alone, as the batched launch uses it
-        with vfe.Mesh(w, stencil=False) as m:
+    for w in models:   # the same kernels per node as in the batch
+        with vfe.Mesh(w) as m:
             m.step(nsteps)
             alone.append((vfe.vfe_get_state(m.handle), m.traces()))
     meshes = [vfe.Mesh(w) for w in models]
@@ -52,6 +54,25 @@ def test_batch_vs_oracle(orc):
         m.close()
 
 
+def test_batch_element_kernel_only_meshes_equal_individual_runs():
+    """Meshes without the stencil kernel: every column-plane in the fused
+    element launch, bit-identical to each mesh alone."""
+    models = _models()[:4]
+    alone = []
+    for w in models:
+        with vfe.Mesh(w, stencil=False) as m:
+            m.step(9)
+            alone.append(m.traces())
+    meshes = [vfe.Mesh(w, stencil=False) for w in models]
+    with vfe.Batch(meshes) as b:
+        b.step(9)
+        b.synchronize()
+        for m, tr in zip(meshes, alone):
+            assert np.array_equal(m.traces(), tr)
+    for m in meshes:
+        m.close()
+
+
 def test_batch_rejects_mixed_paths():
     w = W.random_mesh(80, shape=(4, 4, 4))
     a = vfe.Mesh(w, path=vfe.VFE_PATH_TC)
@@ -68,7 +89,7 @@ def test_batch_fewer_stages_equals_individual_runs():
     models = _models()[:4]
     alone = []
     for w in models:
-        with vfe.Mesh(w, stages=3, stencil=False) as m:
+        with vfe.Mesh(w, stages=3) as m:
             m.step(11)
             alone.append(m.traces())
     meshes = [vfe.Mesh(w, stages=3) for w in models]

@@ -90,7 +90,7 @@ def test_batch_with_mixed_stage_counts_equals_individual_runs():
     stages = [5, 3, 4, 5]
     alone = []
     for w, st in zip(models, stages):
-        with vfe.Mesh(w, stages=st, stencil=False) as m:
+        with vfe.Mesh(w, stages=st) as m:
             m.step(37)
             alone.append(m.traces())
     meshes = [vfe.Mesh(w, stages=st) for w, st in zip(models, stages)]
