@@ -64,8 +64,12 @@ typedef struct vfe_options {
                        surrounding elements share one material as one node
                        stencil per material part (the element products of
                        Eq. GE:TC summed at the node, same integer split); 0
-                       uses the element-by-element kernel everywhere.  The two
-                       agree to the FP64-equivalent bound of the split. */
+                       uses the element-by-element kernel everywhere; 2 also
+                       gives the stencil the runs that touch the x or y faces
+                       of the mesh (a correction launch after it subtracts the
+                       elements outside the mesh at the face nodes), which 1
+                       does on meshes of 8 Mi elements or more.  They agree to
+                       the FP64-equivalent bound of the split. */
   int ctas;         /* TC path: CTAs per kernel launch, i.e. how many pieces the
                        (node column x plane range) work bricks are cut into;
                        0 (default) = one per SM, the most the kernels take */
@@ -190,9 +194,11 @@ int vfe_get_sizes(vfe_mesh *mesh, int64_t *n_nodes, int64_t *n_elements);
 int vfe_get_step_count(vfe_mesh *mesh, int64_t *steps);
 
 /* Kernel launches one step enqueues on the mesh's stream: on the TC path the
- * one-thread prologue, the element kernel (when any column-plane needs it)
- * and the node-stencil kernel (when enabled and some column-plane is
- * uniform); on the FP64 path the prologue and the step kernel.  VFE_EINVAL:
+ * one-thread prologue, the element kernel (when any column-plane needs it),
+ * the node-stencil kernel (when enabled and some column-plane is uniform)
+ * and, on meshes of 8 Mi elements or more, its correction of the nodes on
+ * the x and y faces of the mesh; on the FP64 path the prologue and the step
+ * kernel.  VFE_EINVAL:
  * a NULL argument. */
 int vfe_get_launches_per_step(vfe_mesh *mesh, int *launches);
 

@@ -200,6 +200,10 @@ struct vfe_mesh {
   std::vector<int4> st_segs;
   std::vector<int32_t> st_mat, st_off;
   int st_ctas = 0;
+  // the stencil runs' nodes on the x or y faces of the mesh (see stencil_face_fix)
+  bool faces_on = false;
+  int4 *d_face = nullptr;
+  int n_face = 0;
   int4 *d_st_segs = nullptr;
   int32_t *d_st_mat = nullptr, *d_st_off = nullptr;
   uint16_t *d_Bst = nullptr;
@@ -283,6 +287,9 @@ static TcDevice tc_stencil_device(const vfe_mesh *m, int cur) {
   d.seg_mat = m->d_st_mat;
   d.n_ctas = m->stencil_on ? m->st_ctas : 0;
   d.Bst = m->d_Bst;
+  d.U_cur = m->d_U[cur];  // u^n: the face nodes' correction reads it
+  d.face = m->d_face;
+  d.n_face = m->stencil_on && m->faces_on ? m->n_face : 0;
   d.recv = nullptr;
   d.recv_off = nullptr;
   d.n_rec = 0;
@@ -336,6 +343,7 @@ static int enqueue_step(vfe_mesh *m, int cur) {
     if (m->stencil_on) {
       TcDevice ds = tc_stencil_device(m, cur);
       CUDA_TRY(stencil_launch(m->stream, ds, &m->st_tmap[cur], TC_MODE_STEP));
+      CUDA_TRY(stencil_face_fix(m->stream, ds, TC_MODE_STEP));
     }
   } else {
     src.amp_scale = m->amp;
@@ -423,7 +431,7 @@ int vfe_destroy(vfe_mesh *m) {
                   m->d_seg_off, m->d_inj, m->d_force, m->d_w[0], m->d_w[1],
                   m->d_W[0], m->d_W[1], m->d_all_segs, m->d_all_off, m->d_st_segs,
                   m->d_st_mat, m->d_st_off, m->d_Bst, m->d_elemB, m->d_elemG, m->d_kappa,
-                  m->d_Kkg};
+                  m->d_Kkg, m->d_face};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -466,7 +474,7 @@ int vfe_create_mesh(int nx, int ny, int nz, double h, const int32_t *material_id
     return fail(VFE_EINVAL, "cfl_fraction must be in (0, 1]");
   if (opt.fix_bottom < 0 || opt.fix_bottom > 2)
     return fail(VFE_EINVAL, "fix_bottom must be 0, 1 or 2");
-  if (opt.stencil != 0 && opt.stencil != 1) return fail(VFE_EINVAL, "stencil must be 0 or 1");
+  if (opt.stencil < 0 || opt.stencil > 2) return fail(VFE_EINVAL, "stencil must be 0, 1 or 2");
   if (opt.ctas < 0) return fail(VFE_EINVAL, "ctas must be >= 0");
 
   vfe_mesh *m = new vfe_mesh();
@@ -711,6 +719,8 @@ static int build_segments(vfe_mesh *m) {
   const int nx = m->nx, ny = m->ny, nz = m->nz, TX = m->tiles_x, TY = m->tiles_y;
   const int planes = nz + 1;
   m->stencil_on = m->opt.path == VFE_PATH_TC && m->opt.stencil != 0 && !m->damped && !m->elem_g;
+  m->faces_on = m->stencil_on &&
+                (m->opt.stencil == 2 || (int64_t)nx * ny * nz >= ST_FACE_MIN_ELEMENTS);
   std::vector<int4> all_runs, el_runs, st_runs;
   std::vector<int32_t> st_rmat;
   std::vector<char> forced((size_t)TX * TY * planes, 0);
@@ -729,7 +739,6 @@ static int build_segments(vfe_mesh *m) {
       // elements around the owned nodes: x in [15 tx - 1, 15 tx + 15), y likewise
       const int ex0 = TC_OWN * tx - 1, ex1 = TC_OWN * tx + TC_OWN;
       const int ey0 = TC_OWN * ty - 1, ey1 = TC_OWN * ty + TC_OWN;
-      const bool inside = ex0 >= 0 && ex1 <= nx && ey0 >= 0 && ey1 <= ny;
       const int cx0 = std::max(ex0, 0), cx1 = std::min(ex1, nx);
       const int cy0 = std::max(ey0, 0), cy1 = std::min(ey1, ny);
       for (int ez = 0; ez < nz; ++ez) {  // per element layer: material, -1 void, -2 mixed
@@ -739,7 +748,9 @@ static int build_segments(vfe_mesh *m) {
           for (int ex = cx0; ex < cx1; ++ex)
             if (row[ex] != v) { v = -2; break; }
         }
-        if (!inside && v >= 0) v = -2;  // solid next to the outside
+        // a solid run next to the outside of the mesh stays uniform on large
+        // meshes (stencil_face_fix corrects its nodes on the mesh faces)
+        if (!m->faces_on && !(ex0 >= 0 && ex1 <= nx && ey0 >= 0 && ey1 <= ny) && v >= 0) v = -2;
         layer[ez] = v;
       }
       int run_cls = -3, run_z0 = 0;
@@ -786,6 +797,25 @@ static int build_segments(vfe_mesh *m) {
     m->el_runs = el_runs;
     m->st_runs = st_runs;
     m->st_rmat = st_rmat;
+    // nodes of the stencil runs on the x or y faces: (i, j, k, type | material
+    // << 8), type bits x low, x high, y low, y high in the face table's order
+    std::vector<int4> face;
+    for (size_t q = 0; q < st_runs.size() && m->faces_on; ++q) {
+      const int4 r = st_runs[q];
+      const int i0 = TC_OWN * r.x, i1 = std::min(TC_OWN * r.x + TC_OWN - 1, nx);
+      const int j0 = TC_OWN * r.y, j1 = std::min(TC_OWN * r.y + TC_OWN - 1, ny);
+      if (i0 > 0 && i1 < nx && j0 > 0 && j1 < ny) continue;  // no face node
+      for (int j = j0; j <= j1; ++j)
+        for (int i = i0; i <= i1; ++i) {
+          const int t = (i == 0 ? 1 : 0) | (i == nx ? 2 : 0) | (j == 0 ? 4 : 0) | (j == ny ? 8 : 0);
+          static const int kIdx[16] = {-1, 0, 1, -1, 2, 4, 6, -1, 3, 5, 7, -1, -1, -1, -1, -1};
+          const int type = kIdx[t];
+          if (type < 0) continue;
+          for (int k = r.z; k < r.w; ++k) face.push_back(make_int4(i, j, k, type | (st_rmat[q] << 8)));
+        }
+    }
+    m->n_face = (int)face.size();
+    if ((rc = upload_vec(&m->d_face, face)) != VFE_OK) return rc;
   } else {
     m->segs = all_segs;
     m->seg_off = all_off;
@@ -936,6 +966,60 @@ static int build_tc(vfe_mesh *m) {
             bst[byte / 2] = __half_as_ushort(__float2half(val));
           }
   }
+  // mesh-face table, after the B images (ST_FACE_TAB_OFF): at a node on the
+  // x or y faces of the mesh the stencil's sums include the elements outside
+  // it (their nodes outside hold zero, their nodes on the face do not); per
+  // face type (x low, x high, y low, y high and the four edges) up to 9
+  // offsets of in-mesh nodes with the 3x3 blocks of K^kappa and of Kbar^G
+  // summed over the outside elements, which stencil_face_fix subtracts.
+  // Entry: [0] neighbour offset (dx+1) + 3 (dy+1) + 9 (dz+1), -1 unused;
+  // [1..9] the K^kappa block (row: output component), [10..18] the Kbar^G
+  // block, [19] zero; 9 entries per type.
+  {
+    const int types[8] = {1, 2, 4, 8, 5, 9, 6, 10};  // bits: x low, x high, y low, y high
+    const size_t base = bst.size();
+    bst.resize(base + 8 * 9 * 20, 0);
+    for (int ti = 0; ti < 8; ++ti) {
+      const int t = types[ti];
+      const bool xlo = t & 1, xhi = t & 2, ylo = t & 4, yhi = t & 8;
+      int64_t Gk[27][9] = {}, Gg[27][9] = {};
+      bool used[27] = {};
+      for (int e = 0; e < 8; ++e) {
+        const int o[3] = {-(e & 1), -((e >> 1) & 1), -((e >> 2) & 1)};
+        const bool outside = (xlo && o[0] == -1) || (xhi && o[0] == 0) || (ylo && o[1] == -1) ||
+                             (yhi && o[1] == 0);
+        if (!outside) continue;
+        const int a = -o[0] - 2 * o[1] - 4 * o[2];
+        for (int bn = 0; bn < 8; ++bn) {
+          const int dd[3] = {o[0] + (bn & 1), o[1] + ((bn >> 1) & 1), o[2] + ((bn >> 2) & 1)};
+          if ((xlo && dd[0] < 0) || (xhi && dd[0] > 0) || (ylo && dd[1] < 0) || (yhi && dd[1] > 0))
+            continue;  // a node outside the mesh: zero
+          const int off = (dd[0] + 1) + 3 * (dd[1] + 1) + 9 * (dd[2] + 1);
+          used[off] = true;
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+              Gk[off][3 * i + j] += Ik[(3 * a + i) * 24 + 3 * bn + j];
+              Gg[off][3 * i + j] += Ig[(3 * a + i) * 24 + 3 * bn + j] - (a == bn && i == j ? 128 : 0);
+            }
+        }
+      }
+      int k = 0;
+      for (int off = 0; off < 27; ++off) {
+        if (!used[off]) continue;
+        if (k >= 9) return fail(VFE_EINVAL, "internal: face type %d has more than 9 offsets", t);
+        int16_t *ent = reinterpret_cast<int16_t *>(&bst[base + (size_t)(ti * 9 + k) * 20]);
+        ent[0] = (int16_t)off;
+        for (int q = 0; q < 9; ++q) {
+          ent[1 + q] = (int16_t)Gk[off][q];
+          ent[10 + q] = (int16_t)Gg[off][q];
+        }
+        ++k;
+      }
+      for (; k < 9; ++k) reinterpret_cast<int16_t *>(&bst[base + (size_t)(ti * 9 + k) * 20])[0] = -1;
+    }
+  }
+  if (sizeof(uint16_t) * bst.size() != ST_BST_BYTES)
+    return fail(VFE_EINVAL, "internal: stencil operand buffer size");
   const size_t ubytes = sizeof(int64_t) * 3 * m->comp;
   CUDA_TRY(cudaMalloc(&m->d_U[0], ubytes));
   CUDA_TRY(cudaMalloc(&m->d_U[1], ubytes));
@@ -1259,7 +1343,8 @@ int vfe_get_step_count(vfe_mesh *m, int64_t *steps) {
 int vfe_get_launches_per_step(vfe_mesh *m, int *launches) {
   if (!m || !launches) return fail(VFE_EINVAL, "NULL argument");
   if (m->opt.path == VFE_PATH_TC)
-    *launches = 1 + (tc_device(m, 0).n_ctas > 0 ? 1 : 0) + (m->stencil_on ? 1 : 0);
+    *launches = 1 + (tc_device(m, 0).n_ctas > 0 ? 1 : 0) + (m->stencil_on ? 1 : 0) +
+                (m->stencil_on && m->faces_on && m->n_face > 0 ? 1 : 0);
   else
     *launches = 2;
   return VFE_OK;
@@ -1522,7 +1607,9 @@ static int tc_apply(vfe_mesh *m, const double *u, int mode, std::vector<int64_t>
       TcDevice ds = tc_stencil_device(m, m->cur);
       ds.params = dp;
       ds.S_out = dout;
-      if ((e = stencil_launch(m->stream, ds, &tms, TC_MODE_KU)) != cudaSuccess) {
+      ds.U_cur = dU;
+      if ((e = stencil_launch(m->stream, ds, &tms, TC_MODE_KU)) != cudaSuccess ||
+          (e = stencil_face_fix(m->stream, ds, TC_MODE_KU)) != cudaSuccess) {
         rc = fail(VFE_ECUDA, "node-stencil K u kernel: %s", cudaGetErrorString(e));
         break;
       }
@@ -2162,6 +2249,7 @@ static int batch_enqueue(vfe_batch *b, int parity) {
       d.seg_mat = q.d_mat;
       d.n_ctas = q.n_ctas;
       CUDA_TRY(stencil_launch_ex(b->side[k % ns], d, &m->st_tmap[cur], TC_MODE_STEP, false));
+      CUDA_TRY(stencil_face_fix(b->side[k % ns], d, TC_MODE_STEP));
     }
   }
   for (const vfe_batch::Group &g : b->groups)

@@ -26,6 +26,14 @@
 #define TC_MAX_REC_CTA 64        // receivers handled per CTA work item
 #define ST_BOXX 20               // stencil kernel: TMA box width in x (int64; 160 B)
 #define ST_BOXY 18               // stencil kernel: node rows per box
+// bytes of the node-stencil kernel's operand buffer: 9 B images of 2560 bytes,
+// then the mesh-face table (8 types x 9 entries x 20 int16)
+#define ST_BST_BYTES (9 * 2560 + 8 * 9 * 20 * 2)
+#define ST_FACE_TAB_OFF (9 * 2560)
+// meshes of at least this many elements give the uniform runs that touch the
+// x or y faces to the stencil kernel (one more launch per step corrects their
+// face nodes); smaller meshes leave them to the element kernel
+#define ST_FACE_MIN_ELEMENTS (8LL << 20)
 #define TC_UNITS_BITS 59         // target bit length of max |U| after rescale
                                  // (a step's growth keeps |U| below 2^62)
 
@@ -103,9 +111,15 @@ struct TcDevice {         // everything the TC kernels read (by value)
   int64_t dG, dH, dB;
   int damped;
   // node-stencil kernel (vfe_stencil.cu): its own segments, their material
-  // and its B operand image (9 neighbour rows x 16 x 16 fp16)
+  // and its operand buffer (B images, then the mesh-face table); U_cur above
+  // holds u^n for the face nodes' correction
   const int32_t *seg_mat;
   const uint16_t *Bst;
+  // the nodes of the stencil runs on the x or y faces of the mesh (meshes of
+  // ST_FACE_MIN_ELEMENTS or more), which stencil_face_fix corrects after the
+  // kernel: (i, j, k, type | material << 8)
+  const int4 *face;
+  int n_face;
   // per-element shear modulus (vfe_set_shear_moduli): the element kernel's
   // G multiplier round(G_e ds/384 2^e_ref) per element, or nullptr
   const int64_t *elem_B;
@@ -230,6 +244,10 @@ cudaError_t stencil_prepare();
 cudaError_t stencil_launch(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
 cudaError_t stencil_launch_ex(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode,
                               bool pdl);
+// after a stencil launch (modes STEP and KU): subtract, at the listed nodes on
+// the x and y faces of the mesh, the contributions of the elements outside it
+// that the node stencil includes (u^n from d.U_cur)
+cudaError_t stencil_face_fix(cudaStream_t s, const TcDevice &d, int mode);
 
 cudaError_t tc_state_to_f64(cudaStream_t s, const int64_t *U, const int64_t *persist,
                             int extra_shift, int nx, int ny, int64_t nn, int nxp, int64_t plane,

@@ -77,6 +77,7 @@ constexpr int kUSlots = 8;
 constexpr int kBKStride = 10 * 128;
 constexpr int kBImage = 2 * kBKStride;                    // 2560
 constexpr int kBBytes = 9 * kBImage;
+static_assert(kBBytes == ST_FACE_TAB_OFF, "the host's operand buffer: B images, then the face table");
 // the bias image: 16 K rows x 16 N columns, K rows 12..15 = 12288 (fp16),
 // the rest zero; against the constant 256 in K rows 12..15 of every digit
 // block it gives 4 x 256 x 12288 = 1.5 2^23 in each of the 16 columns
@@ -131,6 +132,128 @@ constexpr uint32_t kHalf256 = 0x5C005C00u;    // two fp16 256.0
 constexpr uint32_t kHalf12288 = 0x72007200u;  // two fp16 12288.0
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Mesh faces.  At a node on the x or y faces of the mesh the node stencil
+// also sums the elements outside the mesh; their nodes outside hold zero, but
+// their nodes on the face carry the field.  One thread per such node (after
+// the stencil kernel, on the same stream) forms, from the same digit values
+// q' the kernel used, the outside elements' parts Pg = sum G^k q', Qg = sum
+// Gbar q' (the face table's 3x3 blocks at up to 9 in-mesh offsets) and the
+// excess identity term (1024 - 128 n_in) q'(n) of Kbar^G, takes the material
+// product dS = -(hi63(A Pg + B Qg) + hi63((1024 - 128 n_in) q'(n) B)) and
+// either adds it to S (K u) or takes its increment off u^{n+1} with the
+// update's own fixed-point arithmetic (time step), folding |u^{n+1}| into
+// the column bounds again.  Within a few units of the state of forming the
+// corrected S at once.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__device__ void face_fix_node(const TcDevice &d, const TcStepParams &P, const int64_t *Un, int gi,
+                              int gj, int z, int type, int A1, int A0, int B1, int B0, int shq) {
+  const int16_t *tab = reinterpret_cast<const int16_t *>(
+                           reinterpret_cast<const unsigned char *>(d.Bst) + ST_FACE_TAB_OFF) +
+                       type * 9 * 20;
+  const int64_t dbias = (1LL << 10) | (1LL << 21) | (1LL << 32) | (1LL << 43) | (1LL << 54);
+  const int lo_bits = TC_DIGIT_BITS * (TC_MAX_STAGES - d.stages);
+  const int64_t dbias_hi = (dbias >> lo_bits) << lo_bits;
+  auto qprime = [&](int64_t u) -> int64_t {
+    const int64_t v = (u >> shq) + dbias;
+    return ((v >> lo_bits) << lo_bits) - dbias_hi;
+  };
+  int64_t pg[3] = {0, 0, 0}, qg[3] = {0, 0, 0};
+  for (int k = 0; k < 9; ++k) {
+    const int off = tab[20 * k];
+    if (off < 0) break;
+    const int dx = off % 3 - 1, dy = (off / 3) % 3 - 1, dz = off / 9 - 1;
+    const int64_t nb = (int64_t)(z + dz) * d.plane + (int64_t)(gj + dy) * d.nxp + (gi + dx);
+    int64_t q[3];
+    for (int j = 0; j < 3; ++j) q[j] = qprime(Un[j * d.comp + nb]);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        pg[i] += (int64_t)tab[20 * k + 1 + 3 * i + j] * q[j];
+        qg[i] += (int64_t)tab[20 * k + 10 + 3 * i + j] * q[j];
+      }
+  }
+  const int n_in = type < 4 ? 4 : 2;  // elements inside: face 4, edge 2
+  const int64_t nidx = (int64_t)z * d.plane + (int64_t)gj * d.nxp + gi;
+  int64_t dS[3];
+  for (int c = 0; c < 3; ++c) {
+    const int64_t qn = qprime(Un[c * d.comp + nidx]);
+    dS[c] = -(mul2_hi63(pg[c], qg[c], A1, A0, B1, B0) + mul_hi63(qn * (1024 - 128 * n_in), B1, B0));
+  }
+  if (MODE == TC_MODE_KU) {
+    for (int c = 0; c < 3; ++c) d.S_out[c * d.comp + nidx] += dS[c];
+    return;
+  }
+  const int64_t cn = d.C[nidx];
+  if (cn == 0) return;  // fixed or massless: left at zero
+  const int Rseg = P.eCref + P.rs - shq - 63;
+  const int C1 = (int)(cn >> 31), C0 = (int)(cn & 0x7FFFFFFF);
+  unsigned long long orv = 0;
+  for (int c = 0; c < 3; ++c) {
+    int64_t du;
+    if (Rseg >= 63) {
+      const int64_t H = mul_hi63(dS[c], C1, C0);
+      const int sh = Rseg - 63;
+      du = sh == 0 ? H : (sh > 62 ? 0 : (H + ((int64_t)1 << (sh - 1))) >> sh);
+    } else if (Rseg > 0) {
+      du = mul_shr_round(dS[c], cn, Rseg);
+    } else {
+      const __int128 prod = (__int128)dS[c] * (__int128)cn;
+      du = (int64_t)(prod << min(-Rseg, 63));
+    }
+    const int64_t un = d.U_next[c * d.comp + nidx] - du;
+    d.U_next[c * d.comp + nidx] = un;
+    orv |= (unsigned long long)(un ^ (un >> 63));
+  }
+  if (orv) {
+    unsigned long long *cur = d.or_slots + (size_t)P.or_slot * (1 + d.tiles_x * d.tiles_y);
+    atomicOr(&cur[1 + (gj / TC_OWN) * d.tiles_x + gi / TC_OWN], orv);
+    atomicOr(&cur[0], orv);
+  }
+}
+
+// one thread per listed face node (i, j, k, type | material << 8), after the
+// stencil kernel on the same stream
+template <int MODE>
+__global__ void __launch_bounds__(256) stencil_face_fix_kernel(const TcDevice d) {
+  const TcStepParams P = *d.params;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < d.n_face;
+       idx += gridDim.x * blockDim.x) {
+    const int4 f = d.face[idx];
+    const int gi = f.x, gj = f.y, z = f.z, type = f.w & 255, mat = f.w >> 8;
+    // the digit shift of the node's column, as the stencil kernel takes it
+    int shq = P.shq;
+    if (MODE == TC_MODE_STEP) {
+      const int tx = gi / TC_OWN, ty = gj / TC_OWN;
+      const unsigned long long *prev =
+          d.or_slots + (size_t)((P.or_slot + 2) % 3) * (1 + d.tiles_x * d.tiles_y) + 1;
+      unsigned long long o = 0;
+      for (int dyc = -1; dyc <= 1; ++dyc)
+        for (int dxc = -1; dxc <= 1; ++dxc) {
+          const int cx = tx + dxc, cy = ty + dyc;
+          if (cx >= 0 && cy >= 0 && cx < d.tiles_x && cy < d.tiles_y) o |= prev[cy * d.tiles_x + cx];
+        }
+      const int b = o ? 64 - __clzll((long long)o) : 0;
+      shq = min(P.shq, max(0, b - TC_QBITS));
+    }
+    const TcMaterial mt = d.mats[mat];
+    face_fix_node<MODE>(d, P, d.U_cur, gi, gj, z, type, (int)(mt.A >> 31), (int)(mt.A & 0x7FFFFFFF),
+                        (int)(mt.B >> 31), (int)(mt.B & 0x7FFFFFFF), shq);
+  }
+}
+
+cudaError_t stencil_face_fix(cudaStream_t s, const TcDevice &d, int mode) {
+  if (d.n_face <= 0 || d.n_ctas <= 0) return cudaSuccess;
+  const int blocks = (d.n_face + 255) / 256 < 1024 ? (d.n_face + 255) / 256 : 1024;
+  if (mode == TC_MODE_STEP)
+    stencil_face_fix_kernel<TC_MODE_STEP><<<blocks, 256, 0, s>>>(d);
+  else if (mode == TC_MODE_KU)
+    stencil_face_fix_kernel<TC_MODE_KU><<<blocks, 256, 0, s>>>(d);
+  else
+    return cudaSuccess;
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------------------
 // MODE: TC_MODE_STEP (time step), TC_MODE_KU (S of K u), TC_MODE_PARTIALS

@@ -439,7 +439,8 @@ class Mesh:
             fix_bottom = workload.get("fix_bottom", 1)
         opt = vfe_default_options(element_kind=kind, path=path, stages=stages, dt=dt,
                                   fix_bottom=int(fix_bottom), device=device,
-                                  stream=stream or 0, stencil=1 if stencil else 0,
+                                  stream=stream or 0,
+                                  stencil=int(stencil) if stencil is not True else 1,
                                   ctas=int(ctas))
         self.handle = vfe_create_mesh(nx, ny, nz, workload["h"], workload["material_ids"],
                                       workload["material_table"], opt)

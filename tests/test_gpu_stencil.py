@@ -7,10 +7,13 @@ part.  Checked here
 
 * bit for bit: the kernel's integer partial sums P = S^k q and S^G q, and the
   node's own q, against exact integer stencils built from the hand-derived
-  closed form of the element (independent of the library);
+  closed form of the element (independent of the library), zero outside the
+  mesh;
 * K u against the FP64 oracle, on meshes with uniform blocks, material
-  interfaces, voids and mesh faces (the last three go to the element kernel),
-  and against the element kernel alone (stencil off);
+  interfaces and voids (these two go to the element kernel) and mesh faces
+  (on meshes of 8 Mi elements or more, a correction after the stencil
+  kernel subtracts the elements outside the mesh at the face nodes), and
+  against the element kernel alone (stencil off);
 * time steps from a state and from rest (source, receivers) against the
   oracle, and the state after steps with the stencil on and off.
 """
@@ -73,11 +76,13 @@ def layered(shape, seed=1, void_top=0, inclusion=True):
 SHAPES = [(47, 40, 12), (33, 31, 20), (64, 33, 9)]
 
 
+@pytest.mark.parametrize("faces", [False, True])
 @pytest.mark.parametrize("shape", SHAPES)
-def test_stencil_partials_bit_exact(shape):
+def test_stencil_partials_bit_exact(shape, faces):
     mesh = layered(shape)
     u = W.random_displacement(mesh, 3)
-    with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False) as m:
+    with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False,
+                  stencil=2 if faces else 1) as m:
         out, cov, sh, F = vfe.vfe_debug_stencil_partials(m.handle, u)
     assert cov.sum() > 0, "the mesh has no uniform run"
     q = (np.rint(np.ldexp(u, F)).astype(np.int64) >> sh).reshape(-1, 3)
@@ -85,13 +90,22 @@ def test_stencil_partials_bit_exact(shape):
     nx, ny, nz = shape
     idx = np.flatnonzero(cov)
     i, j, k = idx % (nx + 1), (idx // (nx + 1)) % (ny + 1), idx // ((nx + 1) * (ny + 1))
+    on_face = (i == 0) | (i == nx) | (j == 0) | (j == ny)
+    if faces:   # face and edge nodes of the mesh are covered too
+        assert ((i == 0) | (i == nx)).any() and ((j == 0) | (j == ny)).any()
+        assert (((i == 0) | (i == nx)) & ((j == 0) | (j == ny))).any()
+    else:
+        assert not on_face.any()
     P = np.zeros((len(idx), 3), dtype=np.int64)
     Q = np.zeros((len(idx), 3), dtype=np.int64)
     for (ox, oy, oz), blk in Sk.items():
-        nb = (i + ox) + (nx + 1) * ((j + oy) + (ny + 1) * (k + oz))
-        P += q[nb] @ blk.T
+        # a neighbour outside the mesh (x or y faces) holds zero
+        inside = (i + ox >= 0) & (i + ox <= nx) & (j + oy >= 0) & (j + oy <= ny)
+        nb = np.where(inside, (i + ox) + (nx + 1) * ((j + oy) + (ny + 1) * (k + oz)), 0)
+        qn = q[nb] * inside[:, None]
+        P += qn @ blk.T
         g = Sg[(ox, oy, oz)] - (1024 * np.eye(3, dtype=np.int64) if (ox, oy, oz) == (0, 0, 0) else 0)
-        Q += q[nb] @ g.T
+        Q += qn @ g.T
     assert np.array_equal(out[idx, 0:3], P)
     assert np.array_equal(out[idx, 3:6], Q)
     assert np.array_equal(out[idx, 6:9], q[idx])
@@ -105,7 +119,7 @@ def test_stencil_ku_matches_oracle(orc, shape, void_top):
     u = W.random_displacement(mesh, 7)
     ref = orc.ku(0, mesh, u)
     res = {}
-    for on in (True, False):
+    for on in (2, True, False):   # with the face nodes, without, element kernel only
         with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False, stencil=on) as m:
             res[on] = m.internal_force(u)
         assert rel_max(res[on], ref) <= KU_TOL, on
@@ -134,6 +148,28 @@ def test_stencil_steps_from_state(orc, nsteps):
             ug, ugm = vfe.vfe_get_state(m.handle)
         assert rel_max(ug, uo) <= 1e-13, on
         assert rel_max(ugm, umo) <= 1e-13, on
+
+
+def test_stencil_face_nodes_steps_from_state(orc):
+    """The stencil kernel on the runs at the mesh faces (stencil=2), its face
+    nodes corrected after it: steps from a state against the oracle."""
+    mesh = layered((47, 40, 12), void_top=2)
+    mass = orc.node_mass(0, mesh)
+    nx, ny, _ = mesh["shape"]
+    free = mass > 0
+    free[: (nx + 1) * (ny + 1)] = False
+    rng = np.random.default_rng(18)
+    u = rng.uniform(-1e-3, 1e-3, 3 * len(mass)) * np.repeat(free, 3)
+    um = u + rng.uniform(-1e-5, 1e-5, len(u)) * np.repeat(free, 3)
+    dt = orc.dt(0, mesh, 0.5)
+    _, uo, umo = orc.run(0, mesh, dt, 5, u0=u, um1=um, return_state=True)
+    with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False, stencil=2) as m:
+        assert vfe.vfe_get_launches_per_step(m.handle) == 4
+        vfe.vfe_set_state(m.handle, u, um)
+        m.step(5)
+        ug, ugm = vfe.vfe_get_state(m.handle)
+    assert rel_max(ug, uo) <= 1e-13
+    assert rel_max(ugm, umo) <= 1e-13
 
 
 def test_stencil_traces_from_rest(orc):
