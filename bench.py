@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--stages", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--stencil", type=int, choices=[0, 1, 2], default=1,
+                    help="TC path node-stencil option: 1 (default: per-node corrections on "
+                         "meshes of 8 Mi elements or more), 2 (on every mesh), 0 (element "
+                         "kernel only)")
     ap.add_argument("--damping", type=float, default=0.0,
                     help="Rayleigh damping ratio h over the source band (100-125 kHz on "
                          "paper_rebar, f0 * [0.89, 1.11] otherwise); 0 = undamped")
@@ -368,7 +372,7 @@ def run_ours(args):
 
     # --- the TC path (headline)
     m = damp(vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stages=args.stages,
-                      stream=stream.cuda_stream, device=local))
+                      stream=stream.cuda_stream, device=local, stencil=args.stencil))
     with ClockSampler(local) as clk:
         total_ms, per = timed_steps(m, args.steps, args.warmup)
     clocks = clk.summary()
@@ -384,7 +388,8 @@ def run_ours(args):
     # memory, queued behind the step (vfe_get_trace_rows_async); the timed
     # region ends when every row has arrived (vfe_synchronize).  The model
     # itself is uploaded once by vfe_create_mesh.
-    m = damp(vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stages=args.stages, device=local))
+    m = damp(vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stages=args.stages, device=local,
+                      stencil=args.stencil))
     ntot = args.warmup + args.steps
     force = torch.empty((ntot, 3), dtype=torch.float64, pin_memory=True).numpy()
     force[:] = ricker_rows(ntot, m.dt, mesh["source"])
@@ -408,6 +413,8 @@ def run_ours(args):
     # --- the plain FP64 CUDA-core path on the same workload, and the trace
     # agreement of the two GPU paths over the same steps
     cfg = workload_config(mesh, args.stages, "TC (exact 11-bit integer digits on tcgen05)")
+    if args.stencil != 1:
+        cfg["stencil_option"] = args.stencil
     if args.damping > 0:
         cfg["rayleigh_damping_ratio"] = args.damping
     if not args.no_fp64:
@@ -425,7 +432,7 @@ def run_ours(args):
         trs = []
         for path in (vfe.VFE_PATH_TC, vfe.VFE_PATH_FP64):
             mp = damp(vfe.Mesh(mesh, path=path, stages=args.stages, stream=stream.cuda_stream,
-                               device=local))
+                               device=local, stencil=args.stencil))
             mp.step(nt)
             trs.append(mp.traces())
             mp.close()

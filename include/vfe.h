@@ -64,12 +64,15 @@ typedef struct vfe_options {
                        surrounding elements share one material as one node
                        stencil per material part (the element products of
                        Eq. GE:TC summed at the node, same integer split); 0
-                       uses the element-by-element kernel everywhere; 2 also
-                       gives the stencil the runs that touch the x or y faces
-                       of the mesh (a correction launch after it subtracts the
-                       elements outside the mesh at the face nodes), which 1
-                       does on meshes of 8 Mi elements or more.  They agree to
-                       the FP64-equivalent bound of the split. */
+                       uses the element-by-element kernel everywhere; 2 gives
+                       the stencil every node plane but those holding the
+                       source or a receiver, each node taking the most
+                       frequent material among its eight elements, and a
+                       correction launch after it exchanges the material of
+                       the node's other elements (another material, void, or
+                       outside the mesh); 1 does the same on meshes of 8 Mi
+                       elements or more.  They agree to the FP64-equivalent
+                       bound of the split. */
   int ctas;         /* TC path: CTAs per kernel launch, i.e. how many pieces the
                        (node column x plane range) work bricks are cut into;
                        0 (default) = one per SM, the most the kernels take */
@@ -195,10 +198,10 @@ int vfe_get_step_count(vfe_mesh *mesh, int64_t *steps);
 
 /* Kernel launches one step enqueues on the mesh's stream: on the TC path the
  * one-thread prologue, the element kernel (when any column-plane needs it),
- * the node-stencil kernel (when enabled and some column-plane is uniform)
- * and, on meshes of 8 Mi elements or more, its correction of the nodes on
- * the x and y faces of the mesh; on the FP64 path the prologue and the step
- * kernel.  VFE_EINVAL:
+ * the node-stencil kernel (when enabled) and, when some node of its runs
+ * has elements of another material than its own, void or outside the mesh
+ * (meshes of 8 Mi elements or more, or stencil option 2), the correction
+ * of those nodes; on the FP64 path the prologue and the step kernel.  VFE_EINVAL:
  * a NULL argument. */
 int vfe_get_launches_per_step(vfe_mesh *mesh, int *launches);
 
@@ -317,8 +320,8 @@ int vfe_set_shear_moduli(vfe_mesh *mesh, const double *G);
  * mesh n steps: per step one prologue launch, one fused element-kernel launch
  * per stage count over those meshes' non-uniform node columns (all of a
  * mesh's columns when its stencil option is off), and for each mesh with
- * the node-stencil kernel one stencil launch over its uniform runs on a
- * share of the SMs in proportion to its size, on side streams that run side
+ * the node-stencil kernel one stencil launch over its stencil runs (and
+ * their correction launch) on a share of the SMs in proportion to its size, on side streams that run side
  * by side; replayed as captured CUDA graphs of 32 and of 2 steps; each mesh
  * keeps its own source, receivers, traces, state and time step.  Work queued
  * on a mesh's own stream before the call runs first; calls on a mesh after it

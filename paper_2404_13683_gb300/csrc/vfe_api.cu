@@ -200,10 +200,14 @@ struct vfe_mesh {
   std::vector<int4> st_segs;
   std::vector<int32_t> st_mat, st_off;
   int st_ctas = 0;
-  // the stencil runs' nodes on the x or y faces of the mesh (see stencil_face_fix)
-  bool faces_on = false;
-  int4 *d_face = nullptr;
-  int n_face = 0;
+  // per-node material and corrections (meshes of ST_FIX_MIN_ELEMENTS or
+  // more, or stencil option 2): every column-plane but the source and
+  // receiver planes goes to the stencil kernel, with the reference material
+  // of each node of its runs and the correction entries of stencil_fix
+  bool fix_on = false;
+  uint8_t *d_node_mat = nullptr;
+  int4 *d_fix = nullptr;
+  int n_fix = 0;
   int4 *d_st_segs = nullptr;
   int32_t *d_st_mat = nullptr, *d_st_off = nullptr;
   uint16_t *d_Bst = nullptr;
@@ -287,9 +291,10 @@ static TcDevice tc_stencil_device(const vfe_mesh *m, int cur) {
   d.seg_mat = m->d_st_mat;
   d.n_ctas = m->stencil_on ? m->st_ctas : 0;
   d.Bst = m->d_Bst;
-  d.U_cur = m->d_U[cur];  // u^n: the face nodes' correction reads it
-  d.face = m->d_face;
-  d.n_face = m->stencil_on && m->faces_on ? m->n_face : 0;
+  d.U_cur = m->d_U[cur];  // u^n: the corrections read it
+  d.node_mat = m->d_node_mat;
+  d.fix = m->d_fix;
+  d.n_fix = m->stencil_on ? m->n_fix : 0;
   d.recv = nullptr;
   d.recv_off = nullptr;
   d.n_rec = 0;
@@ -343,7 +348,7 @@ static int enqueue_step(vfe_mesh *m, int cur) {
     if (m->stencil_on) {
       TcDevice ds = tc_stencil_device(m, cur);
       CUDA_TRY(stencil_launch(m->stream, ds, &m->st_tmap[cur], TC_MODE_STEP));
-      CUDA_TRY(stencil_face_fix(m->stream, ds, TC_MODE_STEP));
+      CUDA_TRY(stencil_fix(m->stream, ds, TC_MODE_STEP));
     }
   } else {
     src.amp_scale = m->amp;
@@ -431,7 +436,7 @@ int vfe_destroy(vfe_mesh *m) {
                   m->d_seg_off, m->d_inj, m->d_force, m->d_w[0], m->d_w[1],
                   m->d_W[0], m->d_W[1], m->d_all_segs, m->d_all_off, m->d_st_segs,
                   m->d_st_mat, m->d_st_off, m->d_Bst, m->d_elemB, m->d_elemG, m->d_kappa,
-                  m->d_Kkg, m->d_face};
+                  m->d_Kkg, m->d_fix, m->d_node_mat};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -707,22 +712,33 @@ static int upload_vec(T **dptr, const std::vector<T> &v) {
   return VFE_OK;
 }
 
-// Work decomposition of the TC path.  Column-plane (15x15 node column, one
-// node plane) classes: uniform material m when every element around the
-// column's nodes on both sides of the plane has material m and the column is
-// inside the mesh (node-stencil kernel); void when every such element is void
-// or outside the mesh (massless nodes stay at rest: no work); mixed otherwise,
-// and always for planes holding the source or a receiver (element kernel).
-// With the node-stencil kernel off (option, or Rayleigh damping) every
-// column-plane goes to the element kernel, as does the exact-partials list.
+// Work decomposition of the TC path.  A column-plane (15x15 node column, one
+// node plane) is void when every element around the column's nodes on both
+// sides of the plane is void or outside the mesh (massless nodes stay at
+// rest: no work).  With per-node corrections (fix_on) every other
+// column-plane goes to the node-stencil kernel, but for the planes holding
+// the source or a receiver (element kernel); without them only the uniform
+// ones do (every element around the column's nodes of material m, the column
+// inside the mesh, not the end planes) and mixed planes go to the element
+// kernel.  A stencil run of one plane goes to the element kernel.  With the
+// node-stencil kernel off (option, or Rayleigh damping) every column-plane
+// goes to the element kernel, as does the exact-partials list.
 static int build_segments(vfe_mesh *m) {
   const int nx = m->nx, ny = m->ny, nz = m->nz, TX = m->tiles_x, TY = m->tiles_y;
   const int planes = nz + 1;
   m->stencil_on = m->opt.path == VFE_PATH_TC && m->opt.stencil != 0 && !m->damped && !m->elem_g;
-  m->faces_on = m->stencil_on &&
-                (m->opt.stencil == 2 || (int64_t)nx * ny * nz >= ST_FACE_MIN_ELEMENTS);
+  m->fix_on = m->stencil_on &&
+               (m->opt.stencil == 2 || (int64_t)nx * ny * nz >= ST_FIX_MIN_ELEMENTS);
   std::vector<int4> all_runs, el_runs, st_runs;
   std::vector<int32_t> st_rmat;
+  // the stencil runs' nodes: reference material, correction entries
+  std::vector<uint8_t> node_mat(m->stencil_on ? (size_t)m->comp : 0, (uint8_t)ST_NO_MAT);
+  std::vector<int4> fix;
+  auto elem_mat = [&](int ex, int ey, int ez) -> int {  // material; -1 void or outside
+    if (ex < 0 || ey < 0 || ez < 0 || ex >= nx || ey >= ny || ez >= nz) return -1;
+    const int v = m->mat[(size_t)ex + (size_t)nx * (ey + (size_t)ny * ez)];
+    return v < 0 ? -1 : v;
+  };
   std::vector<char> forced((size_t)TX * TY * planes, 0);
   auto force = [&](int64_t n) {
     const int i = (int)(n % (nx + 1)), j = (int)((n / (nx + 1)) % (ny + 1));
@@ -748,9 +764,8 @@ static int build_segments(vfe_mesh *m) {
           for (int ex = cx0; ex < cx1; ++ex)
             if (row[ex] != v) { v = -2; break; }
         }
-        // a solid run next to the outside of the mesh stays uniform on large
-        // meshes (stencil_face_fix corrects its nodes on the mesh faces)
-        if (!m->faces_on && !(ex0 >= 0 && ex1 <= nx && ey0 >= 0 && ey1 <= ny) && v >= 0) v = -2;
+        // without corrections a column at the x or y faces is not uniform
+        if (!m->fix_on && !(ex0 >= 0 && ex1 <= nx && ey0 >= 0 && ey1 <= ny) && v >= 0) v = -2;
         layer[ez] = v;
       }
       int run_cls = -3, run_z0 = 0;
@@ -769,11 +784,17 @@ static int build_segments(vfe_mesh *m) {
             el_runs.push_back(make_int4(tx, ty, run_z0, z1));
         }
       };
+      const size_t st_first = st_runs.size();
       for (int L = 0; L < planes; ++L) {
         const int a = L > 0 ? layer[L - 1] : -1, b = L < nz ? layer[L] : -1;
-        int cls = a == b ? a : -2;
+        int cls;
+        if (m->fix_on) {
+          cls = a == -1 && b == -1 ? -1 : 0;  // 0: stencil, per-node material
+        } else {
+          cls = a == b ? a : -2;
+          if (cls >= 0 && (L == 0 || L == nz)) cls = -2;
+        }
         if (forced[((size_t)ty * TX + tx) * planes + L]) cls = -2;
-        if (cls >= 0 && (L == 0 || L == nz)) cls = -2;
         if (cls != run_cls) {
           flush(L);
           run_cls = cls;
@@ -781,6 +802,53 @@ static int build_segments(vfe_mesh *m) {
         }
       }
       flush(planes);
+      // the nodes of this column's stencil runs: the reference material is
+      // the most frequent material among the node's eight elements (the
+      // first in octant order on a tie); each other value among them (a
+      // material, or absent: void or outside) is one correction entry
+      for (size_t q = st_first; q < st_runs.size(); ++q) {
+        const int4 r = st_runs[q];
+        const int i0 = TC_OWN * tx, i1 = std::min(TC_OWN * tx + TC_OWN - 1, nx);
+        const int j0 = TC_OWN * ty, j1 = std::min(TC_OWN * ty + TC_OWN - 1, ny);
+        for (int k = r.z; k < r.w; ++k) {
+          // both element layers uniform: the column's inner nodes need nothing
+          const bool flat = k >= 1 && k < nz && layer[k - 1] >= 0 && layer[k - 1] == layer[k];
+          for (int j = j0; j <= j1; ++j)
+            for (int i = i0; i <= i1; ++i) {
+              const size_t n = (size_t)k * m->plane + (size_t)j * m->nxp + i;
+              if (flat && i > 0 && i < nx && j > 0 && j < ny) {
+                node_mat[n] = (uint8_t)layer[k];
+                continue;
+              }
+              int v[8];
+              for (int o = 0; o < 8; ++o)
+                v[o] = elem_mat(i - (o & 1), j - ((o >> 1) & 1), k - (o >> 2));
+              int ref = -1, best = 0;
+              for (int o = 0; o < 8; ++o) {
+                if (v[o] < 0) continue;
+                int c = 0;
+                for (int p = 0; p < 8; ++p) c += v[p] == v[o];
+                if (c > best) {
+                  best = c;
+                  ref = v[o];
+                }
+              }
+              if (ref < 0) continue;  // no solid element: zero material, no entry
+              node_mat[n] = (uint8_t)ref;
+              int done = 0, cont = 0;
+              for (int o = 0; o < 8; ++o) {
+                if ((done >> o) & 1) continue;
+                int mask = 0;
+                for (int p = 0; p < 8; ++p) mask |= (v[p] == v[o]) << p;
+                done |= mask;
+                if (v[o] == ref) continue;
+                const int f = v[o] < 0 ? ST_NO_MAT : v[o];
+                fix.push_back(make_int4(i, j, k, mask | (f << 8) | (ref << 16) | cont));
+                cont = ST_FIX_CONT;
+              }
+            }
+        }
+      }
     }
   // CTAs per launch: one per SM unless the options ask for fewer
   const int ctas = m->opt.ctas > 0 ? std::min(m->opt.ctas, m->sms) : m->sms;
@@ -797,25 +865,14 @@ static int build_segments(vfe_mesh *m) {
     m->el_runs = el_runs;
     m->st_runs = st_runs;
     m->st_rmat = st_rmat;
-    // nodes of the stencil runs on the x or y faces: (i, j, k, type | material
-    // << 8), type bits x low, x high, y low, y high in the face table's order
-    std::vector<int4> face;
-    for (size_t q = 0; q < st_runs.size() && m->faces_on; ++q) {
-      const int4 r = st_runs[q];
-      const int i0 = TC_OWN * r.x, i1 = std::min(TC_OWN * r.x + TC_OWN - 1, nx);
-      const int j0 = TC_OWN * r.y, j1 = std::min(TC_OWN * r.y + TC_OWN - 1, ny);
-      if (i0 > 0 && i1 < nx && j0 > 0 && j1 < ny) continue;  // no face node
-      for (int j = j0; j <= j1; ++j)
-        for (int i = i0; i <= i1; ++i) {
-          const int t = (i == 0 ? 1 : 0) | (i == nx ? 2 : 0) | (j == 0 ? 4 : 0) | (j == ny ? 8 : 0);
-          static const int kIdx[16] = {-1, 0, 1, -1, 2, 4, 6, -1, 3, 5, 7, -1, -1, -1, -1, -1};
-          const int type = kIdx[t];
-          if (type < 0) continue;
-          for (int k = r.z; k < r.w; ++k) face.push_back(make_int4(i, j, k, type | (st_rmat[q] << 8)));
-        }
-    }
-    m->n_face = (int)face.size();
-    if ((rc = upload_vec(&m->d_face, face)) != VFE_OK) return rc;
+    if (fix.size() > (size_t)INT32_MAX) return fail(VFE_EINVAL, "too many correction entries");
+    for (const int4 &e : fix)
+      if (e.x < 0 || e.x > nx || e.y < 0 || e.y > ny || e.z < 0 || e.z > nz ||
+          ((e.w >> 8) & 255) > ST_NO_MAT || ((e.w >> 16) & 255) >= m->n_mat)
+        return fail(VFE_EINVAL, "internal: correction entry out of range");
+    m->n_fix = (int)fix.size();
+    if ((rc = upload_vec(&m->d_fix, fix)) != VFE_OK) return rc;
+    if ((rc = upload_vec(&m->d_node_mat, node_mat)) != VFE_OK) return rc;
   } else {
     m->segs = all_segs;
     m->seg_off = all_off;
@@ -825,9 +882,26 @@ static int build_segments(vfe_mesh *m) {
     m->st_segs.clear();
     m->st_mat.clear();
     m->st_off.assign(1, 0);
+    m->n_fix = 0;
   }
   m->n_ctas = (int)m->seg_off.size() - 1;
   m->st_ctas = (int)m->st_off.size() - 1;
+  // the kernels index global memory from these tables: check them here
+  auto bad_segs = [&](const std::vector<int4> &segs, const std::vector<int32_t> &off,
+                      int min_planes) {
+    if (off.empty() || off.front() != 0 || off.back() != (int32_t)segs.size()) return true;
+    for (size_t b = 1; b < off.size(); ++b)
+      if (off[b] < off[b - 1]) return true;
+    for (const int4 &q : segs)
+      if (q.x < 0 || q.x >= TX || q.y < 0 || q.y >= TY || q.z < 0 || q.w > planes ||
+          q.w - q.z < min_planes)
+        return true;
+    return false;
+  };
+  if (bad_segs(m->segs, m->seg_off, 1) || (m->stencil_on && bad_segs(m->st_segs, m->st_off, 2)))
+    return fail(VFE_EINVAL, "internal: inconsistent segment tables");
+  if (m->stencil_on && m->st_mat.size() != m->st_segs.size())
+    return fail(VFE_EINVAL, "internal: inconsistent segment tables");
   if ((rc = upload_vec(&m->d_segs, m->segs)) != VFE_OK) return rc;
   if ((rc = upload_vec(&m->d_seg_off, m->seg_off)) != VFE_OK) return rc;
   if ((rc = upload_vec(&m->d_st_segs, m->st_segs)) != VFE_OK) return rc;
@@ -966,35 +1040,29 @@ static int build_tc(vfe_mesh *m) {
             bst[byte / 2] = __half_as_ushort(__float2half(val));
           }
   }
-  // mesh-face table, after the B images (ST_FACE_TAB_OFF): at a node on the
-  // x or y faces of the mesh the stencil's sums include the elements outside
-  // it (their nodes outside hold zero, their nodes on the face do not); per
-  // face type (x low, x high, y low, y high and the four edges) up to 9
-  // offsets of in-mesh nodes with the 3x3 blocks of K^kappa and of Kbar^G
-  // summed over the outside elements, which stencil_face_fix subtracts.
-  // Entry: [0] neighbour offset (dx+1) + 3 (dy+1) + 9 (dz+1), -1 unused;
-  // [1..9] the K^kappa block (row: output component), [10..18] the Kbar^G
-  // block, [19] zero; 9 entries per type.
+  // correction table, after the B images (ST_MASK_IDX_OFF): for every octant
+  // mask M of the eight elements around a node (bit o: element origin
+  // (i - (o & 1), j - (o >> 1 & 1), k - (o >> 2))), the neighbour offsets the
+  // mask's elements reach, each with the 3x3 blocks of K^kappa and of Kbar^G
+  // (the node's rows, the neighbour's columns) summed over those elements,
+  // which stencil_fix applies.  Index: per mask, first row and row count;
+  // row: [0] offset (dx+1) + 3 (dy+1) + 9 (dz+1), [1..9] the K^kappa block
+  // (row: output component), [10..18] the Kbar^G block, [19] zero.
   {
-    const int types[8] = {1, 2, 4, 8, 5, 9, 6, 10};  // bits: x low, x high, y low, y high
-    const size_t base = bst.size();
-    bst.resize(base + 8 * 9 * 20, 0);
-    for (int ti = 0; ti < 8; ++ti) {
-      const int t = types[ti];
-      const bool xlo = t & 1, xhi = t & 2, ylo = t & 4, yhi = t & 8;
+    const size_t idx_base = bst.size();
+    bst.resize(idx_base + 256 * 2, 0);
+    const size_t row_base = bst.size();
+    int rows = 0;
+    for (int mask = 0; mask < 256; ++mask) {
       int64_t Gk[27][9] = {}, Gg[27][9] = {};
       bool used[27] = {};
       for (int e = 0; e < 8; ++e) {
-        const int o[3] = {-(e & 1), -((e >> 1) & 1), -((e >> 2) & 1)};
-        const bool outside = (xlo && o[0] == -1) || (xhi && o[0] == 0) || (ylo && o[1] == -1) ||
-                             (yhi && o[1] == 0);
-        if (!outside) continue;
-        const int a = -o[0] - 2 * o[1] - 4 * o[2];
+        if (!(mask >> e & 1)) continue;
+        const int o[3] = {-(e & 1), -((e >> 1) & 1), -((e >> 2) & 1)};  // element origin
+        const int a = -o[0] - 2 * o[1] - 4 * o[2];                       // the node's corner
         for (int bn = 0; bn < 8; ++bn) {
-          const int dd[3] = {o[0] + (bn & 1), o[1] + ((bn >> 1) & 1), o[2] + ((bn >> 2) & 1)};
-          if ((xlo && dd[0] < 0) || (xhi && dd[0] > 0) || (ylo && dd[1] < 0) || (yhi && dd[1] > 0))
-            continue;  // a node outside the mesh: zero
-          const int off = (dd[0] + 1) + 3 * (dd[1] + 1) + 9 * (dd[2] + 1);
+          const int off = (o[0] + (bn & 1) + 1) + 3 * (o[1] + ((bn >> 1) & 1) + 1) +
+                          9 * (o[2] + ((bn >> 2) & 1) + 1);
           used[off] = true;
           for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) {
@@ -1003,20 +1071,34 @@ static int build_tc(vfe_mesh *m) {
             }
         }
       }
-      int k = 0;
+      // |P_M|, |Q_M| < row L1 x 2^51 must stay below 2^63
+      for (int i = 0; i < 3; ++i) {
+        int64_t rk = 0, rg = 0;
+        for (int off = 0; off < 27; ++off)
+          for (int j = 0; j < 3; ++j) {
+            rk += std::llabs(Gk[off][3 * i + j]);
+            rg += std::llabs(Gg[off][3 * i + j]);
+          }
+        if (std::max(rk, rg) >= 4096) return fail(VFE_EINVAL, "internal: correction row norm");
+      }
+      const int first = rows;
       for (int off = 0; off < 27; ++off) {
         if (!used[off]) continue;
-        if (k >= 9) return fail(VFE_EINVAL, "internal: face type %d has more than 9 offsets", t);
-        int16_t *ent = reinterpret_cast<int16_t *>(&bst[base + (size_t)(ti * 9 + k) * 20]);
+        if (rows >= ST_MASK_ROWS) return fail(VFE_EINVAL, "internal: correction table size");
+        bst.resize(row_base + (size_t)(rows + 1) * 20, 0);
+        int16_t *ent = reinterpret_cast<int16_t *>(&bst[row_base + (size_t)rows * 20]);
         ent[0] = (int16_t)off;
         for (int q = 0; q < 9; ++q) {
           ent[1 + q] = (int16_t)Gk[off][q];
           ent[10 + q] = (int16_t)Gg[off][q];
         }
-        ++k;
+        ++rows;
       }
-      for (; k < 9; ++k) reinterpret_cast<int16_t *>(&bst[base + (size_t)(ti * 9 + k) * 20])[0] = -1;
+      int16_t *ix = reinterpret_cast<int16_t *>(&bst[idx_base + 2 * (size_t)mask]);
+      ix[0] = (int16_t)first;
+      ix[1] = (int16_t)(rows - first);
     }
+    if (rows != ST_MASK_ROWS) return fail(VFE_EINVAL, "internal: correction table size");
   }
   if (sizeof(uint16_t) * bst.size() != ST_BST_BYTES)
     return fail(VFE_EINVAL, "internal: stencil operand buffer size");
@@ -1025,7 +1107,9 @@ static int build_tc(vfe_mesh *m) {
   CUDA_TRY(cudaMalloc(&m->d_U[1], ubytes));
   CUDA_TRY(cudaMalloc(&m->d_C, sizeof(int64_t) * C.size()));
   CUDA_TRY(cudaMalloc(&m->d_Bop, sizeof(uint16_t) * bop.size()));
-  CUDA_TRY(cudaMalloc(&m->d_mats, sizeof(TcMaterial) * mats.size()));
+  // TC_MAX_MAT + 1 entries, zero beyond n_mat (ST_NO_MAT: no solid element)
+  CUDA_TRY(cudaMalloc(&m->d_mats, sizeof(TcMaterial) * (TC_MAX_MAT + 1)));
+  CUDA_TRY(cudaMemset(m->d_mats, 0, sizeof(TcMaterial) * (TC_MAX_MAT + 1)));
   const size_t or_words = 3 * (1 + (size_t)m->tiles_x * m->tiles_y);
   CUDA_TRY(cudaMalloc(&m->d_or, sizeof(unsigned long long) * or_words));
   CUDA_TRY(cudaMalloc(&m->d_tcparams, sizeof(TcStepParams)));
@@ -1344,7 +1428,7 @@ int vfe_get_launches_per_step(vfe_mesh *m, int *launches) {
   if (!m || !launches) return fail(VFE_EINVAL, "NULL argument");
   if (m->opt.path == VFE_PATH_TC)
     *launches = 1 + (tc_device(m, 0).n_ctas > 0 ? 1 : 0) + (m->stencil_on ? 1 : 0) +
-                (m->stencil_on && m->faces_on && m->n_face > 0 ? 1 : 0);
+                (m->stencil_on && m->n_fix > 0 ? 1 : 0);
   else
     *launches = 2;
   return VFE_OK;
@@ -1609,7 +1693,7 @@ static int tc_apply(vfe_mesh *m, const double *u, int mode, std::vector<int64_t>
       ds.S_out = dout;
       ds.U_cur = dU;
       if ((e = stencil_launch(m->stream, ds, &tms, TC_MODE_KU)) != cudaSuccess ||
-          (e = stencil_face_fix(m->stream, ds, TC_MODE_KU)) != cudaSuccess) {
+          (e = stencil_fix(m->stream, ds, TC_MODE_KU)) != cudaSuccess) {
         rc = fail(VFE_ECUDA, "node-stencil K u kernel: %s", cudaGetErrorString(e));
         break;
       }
@@ -2249,7 +2333,7 @@ static int batch_enqueue(vfe_batch *b, int parity) {
       d.seg_mat = q.d_mat;
       d.n_ctas = q.n_ctas;
       CUDA_TRY(stencil_launch_ex(b->side[k % ns], d, &m->st_tmap[cur], TC_MODE_STEP, false));
-      CUDA_TRY(stencil_face_fix(b->side[k % ns], d, TC_MODE_STEP));
+      CUDA_TRY(stencil_fix(b->side[k % ns], d, TC_MODE_STEP));
     }
   }
   for (const vfe_batch::Group &g : b->groups)

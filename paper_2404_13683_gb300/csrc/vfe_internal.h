@@ -26,14 +26,29 @@
 #define TC_MAX_REC_CTA 64        // receivers handled per CTA work item
 #define ST_BOXX 20               // stencil kernel: TMA box width in x (int64; 160 B)
 #define ST_BOXY 18               // stencil kernel: node rows per box
-// bytes of the node-stencil kernel's operand buffer: 9 B images of 2560 bytes,
-// then the mesh-face table (8 types x 9 entries x 20 int16)
-#define ST_BST_BYTES (9 * 2560 + 8 * 9 * 20 * 2)
-#define ST_FACE_TAB_OFF (9 * 2560)
-// meshes of at least this many elements give the uniform runs that touch the
-// x or y faces to the stencil kernel (one more launch per step corrects their
-// face nodes); smaller meshes leave them to the element kernel
-#define ST_FACE_MIN_ELEMENTS (8LL << 20)
+// the node-stencil kernel's operand buffer: 9 B images of 2560 bytes, then
+// the correction table: per octant mask (256 x int16 pairs: first row, rows)
+// and ST_MASK_ROWS rows of 20 int16 (neighbour offset, 3x3 K^kappa block,
+// 3x3 Kbar^G block, zero) summed over the mask's elements
+#define ST_MASK_ROWS 5023
+#define ST_MASK_IDX_OFF (9 * 2560)
+#define ST_MASK_ROW_OFF (ST_MASK_IDX_OFF + 256 * 2 * 2)
+#define ST_BST_BYTES (ST_MASK_ROW_OFF + ST_MASK_ROWS * 20 * 2)
+// meshes of at least this many elements give every column-plane but the
+// source and receiver planes to the stencil kernel, with per-node material
+// and a correction launch for the nodes whose eight elements are not all of
+// that material (material and void interfaces, the mesh faces); smaller
+// meshes give it the uniform runs alone (no correction launch)
+#define ST_FIX_MIN_ELEMENTS (8LL << 20)
+// per-node reference material of the stencil kernel: a material index, or
+// ST_NO_MAT (no solid element; the material table's zero entry)
+#define ST_NO_MAT TC_MAX_MAT
+// correction entry (i, j, k, code): code bits 0-7 the octant mask of the
+// elements to correct (bit o: element origin (i - (o & 1), j - (o >> 1 & 1),
+// k - (o >> 2))), 8-15 their material (ST_NO_MAT: absent), 16-23 the
+// node's reference material, bit 24 set when the entry continues the
+// previous entry's node
+#define ST_FIX_CONT (1 << 24)
 #define TC_UNITS_BITS 59         // target bit length of max |U| after rescale
                                  // (a step's growth keeps |U| below 2^62)
 
@@ -110,16 +125,17 @@ struct TcDevice {         // everything the TC kernels read (by value)
   int64_t *W_next;
   int64_t dG, dH, dB;
   int damped;
-  // node-stencil kernel (vfe_stencil.cu): its own segments, their material
-  // and its operand buffer (B images, then the mesh-face table); U_cur above
-  // holds u^n for the face nodes' correction
+  // node-stencil kernel (vfe_stencil.cu): its own segments and operand
+  // buffer (B images, then the correction table), the reference material of
+  // every node of its runs (mats[] has TC_MAX_MAT + 1 entries, zero beyond
+  // n_mat); U_cur above holds u^n for the corrections
   const int32_t *seg_mat;
   const uint16_t *Bst;
-  // the nodes of the stencil runs on the x or y faces of the mesh (meshes of
-  // ST_FACE_MIN_ELEMENTS or more), which stencil_face_fix corrects after the
-  // kernel: (i, j, k, type | material << 8)
-  const int4 *face;
-  int n_face;
+  const uint8_t *node_mat;
+  // the correction entries of the stencil runs' nodes (stencil_fix, after
+  // the kernel)
+  const int4 *fix;
+  int n_fix;
   // per-element shear modulus (vfe_set_shear_moduli): the element kernel's
   // G multiplier round(G_e ds/384 2^e_ref) per element, or nullptr
   const int64_t *elem_B;
@@ -244,10 +260,11 @@ cudaError_t stencil_prepare();
 cudaError_t stencil_launch(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
 cudaError_t stencil_launch_ex(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode,
                               bool pdl);
-// after a stencil launch (modes STEP and KU): subtract, at the listed nodes on
-// the x and y faces of the mesh, the contributions of the elements outside it
-// that the node stencil includes (u^n from d.U_cur)
-cudaError_t stencil_face_fix(cudaStream_t s, const TcDevice &d, int mode);
+// after a stencil launch (modes STEP and KU): at the listed nodes, replace
+// the contributions of the elements that are not of the node's reference
+// material (another material, void, outside the mesh) that the node stencil
+// includes (u^n from d.U_cur)
+cudaError_t stencil_fix(cudaStream_t s, const TcDevice &d, int mode);
 
 cudaError_t tc_state_to_f64(cudaStream_t s, const int64_t *U, const int64_t *persist,
                             int extra_shift, int nx, int ny, int64_t nn, int nxp, int64_t plane,

@@ -208,9 +208,9 @@ int vfe_internal_force_noalloc(vfe_mesh *mesh, const double *u, double *f) {
     TcDevice ds = v.st;
     ds.params = params;
     ds.S_out = regB;
-    ds.U_cur = regA;  // u^n for the face nodes' correction
+    ds.U_cur = regA;  // u^n for the per-node corrections
     NA_TRY(stencil_launch(s, ds, &smap, TC_MODE_KU));
-    NA_TRY(stencil_face_fix(s, ds, TC_MODE_KU));
+    NA_TRY(stencil_fix(s, ds, TC_MODE_KU));
   }
   // S -> f (FP64 AoS) in region A, then to the caller
   noalloc_from_fixed_kernel<<<blocks, threads, 0, s>>>(regB, v.nx, v.ny, v.nn, v.nxp, v.plane,

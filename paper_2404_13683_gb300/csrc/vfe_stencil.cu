@@ -77,7 +77,7 @@ constexpr int kUSlots = 8;
 constexpr int kBKStride = 10 * 128;
 constexpr int kBImage = 2 * kBKStride;                    // 2560
 constexpr int kBBytes = 9 * kBImage;
-static_assert(kBBytes == ST_FACE_TAB_OFF, "the host's operand buffer: B images, then the face table");
+static_assert(kBBytes == ST_MASK_IDX_OFF, "the host's operand buffer: B images, then the correction table");
 // the bias image: 16 K rows x 16 N columns, K rows 12..15 = 12288 (fp16),
 // the rest zero; against the constant 256 in K rows 12..15 of every digit
 // block it gives 4 x 256 x 12288 = 1.5 2^23 in each of the 16 columns
@@ -95,9 +95,13 @@ constexpr int kSegInfoBytes = 48;
 constexpr int kOffSeg = kOffBias + kBiasBytes;
 constexpr int kOffBar = kOffSeg + kSegCap * kSegInfoBytes;
 constexpr int kOffMisc = kOffBar + 16 * 8;
-constexpr int kSmemBytes = kOffMisc + 64;
+// the material multipliers as 31-bit limbs {A1, A0, B1, B0}, per material
+// index 0 .. TC_MAX_MAT (ST_NO_MAT: zero)
+constexpr int kOffLimb = kOffMisc + 64;
+constexpr int kSmemBytes = kOffLimb + (TC_MAX_MAT + 1) * 16;
 
 static_assert(kOffU % 128 == 0 && kUStride % 128 == 0, "TMA destinations 128-byte aligned");
+static_assert(kOffLimb % 16 == 0, "limb table alignment");
 static_assert(kDSlotBytes % 256 == 0 && kOffB % 128 == 0 && kOffBias % 128 == 0 &&
                   kOffBar % 8 == 0,
               "alignment");
@@ -134,59 +138,99 @@ constexpr uint32_t kHalf12288 = 0x72007200u;  // two fp16 12288.0
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Mesh faces.  At a node on the x or y faces of the mesh the node stencil
-// also sums the elements outside the mesh; their nodes outside hold zero, but
-// their nodes on the face carry the field.  One thread per such node (after
-// the stencil kernel, on the same stream) forms, from the same digit values
-// q' the kernel used, the outside elements' parts Pg = sum G^k q', Qg = sum
-// Gbar q' (the face table's 3x3 blocks at up to 9 in-mesh offsets) and the
-// excess identity term (1024 - 128 n_in) q'(n) of Kbar^G, takes the material
-// product dS = -(hi63(A Pg + B Qg) + hi63((1024 - 128 n_in) q'(n) B)) and
-// either adds it to S (K u) or takes its increment off u^{n+1} with the
-// update's own fixed-point arithmetic (time step), folding |u^{n+1}| into
-// the column bounds again.  Within a few units of the state of forming the
-// corrected S at once.
+// Per-node corrections.  The stencil kernel forms every node of its runs as
+// if the eight elements around it were all of the node's reference material
+// (node_mat; the material table's zero entry where the node has no solid
+// element).  Where some of them are of another material, void or outside the
+// mesh, one thread per such node (after the stencil kernel, on the same
+// stream) forms, from the digit values q' the kernel used, the parts
+// P_M = sum over the elements of octant mask M of their K^kappa rows at the
+// node times q', Q_M the same with Kbar^G (the correction table's 3x3 blocks
+// at the neighbour offsets the mask's elements reach; a neighbour outside
+// the mesh holds zero, as in the kernel), and the identity term
+// 128 |M| q'(n) of K^G', and exchanges the material of those elements:
+//   dS = hi63(A_f P_M + B_f Q_M) + hi63(128 |M| q'(n) B_f) - (the same with A_r, B_r),
+// f the elements' material (zero multipliers where absent), r the node's.
+// The sum over the node's entries is added to S (K u) or its increment is
+// taken off u^{n+1} with the update's own fixed-point arithmetic (time step),
+// folding |u^{n+1}| into the column bounds again: within a few units of
+// forming the corrected S at once.
 // ---------------------------------------------------------------------------
+// the corrections of the node whose first entry is fix[e0]; time step:
+// returns the OR of |u^{n+1}| over its components and sets its column
 template <int MODE>
-__device__ void face_fix_node(const TcDevice &d, const TcStepParams &P, const int64_t *Un, int gi,
-                              int gj, int z, int type, int A1, int A0, int B1, int B0, int shq) {
-  const int16_t *tab = reinterpret_cast<const int16_t *>(
-                           reinterpret_cast<const unsigned char *>(d.Bst) + ST_FACE_TAB_OFF) +
-                       type * 9 * 20;
+__device__ __forceinline__ unsigned long long fix_node(const TcDevice &d, const TcStepParams &P,
+                                                      int e0, int4 f, int &col) {
+  const int16_t *mask_idx = reinterpret_cast<const int16_t *>(
+      reinterpret_cast<const unsigned char *>(d.Bst) + ST_MASK_IDX_OFF);
+  const int16_t *mask_rows = reinterpret_cast<const int16_t *>(
+      reinterpret_cast<const unsigned char *>(d.Bst) + ST_MASK_ROW_OFF);
   const int64_t dbias = (1LL << 10) | (1LL << 21) | (1LL << 32) | (1LL << 43) | (1LL << 54);
   const int lo_bits = TC_DIGIT_BITS * (TC_MAX_STAGES - d.stages);
   const int64_t dbias_hi = (dbias >> lo_bits) << lo_bits;
+  const int64_t *Un = d.U_cur;
+  const int gi = f.x, gj = f.y, z = f.z;
+  // the digit shift of the node's column, as the stencil kernel takes it
+  int shq = P.shq;
+  if (MODE == TC_MODE_STEP) {
+    const int tx = gi / TC_OWN, ty = gj / TC_OWN;
+    const unsigned long long *prev =
+        d.or_slots + (size_t)((P.or_slot + 2) % 3) * (1 + d.tiles_x * d.tiles_y) + 1;
+    unsigned long long o = 0;
+    for (int dyc = -1; dyc <= 1; ++dyc)
+      for (int dxc = -1; dxc <= 1; ++dxc) {
+        const int cx = tx + dxc, cy = ty + dyc;
+        if (cx >= 0 && cy >= 0 && cx < d.tiles_x && cy < d.tiles_y) o |= prev[cy * d.tiles_x + cx];
+      }
+    const int b = o ? 64 - __clzll((long long)o) : 0;
+    shq = min(P.shq, max(0, b - TC_QBITS));
+  }
   auto qprime = [&](int64_t u) -> int64_t {
     const int64_t v = (u >> shq) + dbias;
     return ((v >> lo_bits) << lo_bits) - dbias_hi;
   };
-  int64_t pg[3] = {0, 0, 0}, qg[3] = {0, 0, 0};
-  for (int k = 0; k < 9; ++k) {
-    const int off = tab[20 * k];
-    if (off < 0) break;
-    const int dx = off % 3 - 1, dy = (off / 3) % 3 - 1, dz = off / 9 - 1;
-    const int64_t nb = (int64_t)(z + dz) * d.plane + (int64_t)(gj + dy) * d.nxp + (gi + dx);
-    int64_t q[3];
-    for (int j = 0; j < 3; ++j) q[j] = qprime(Un[j * d.comp + nb]);
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        pg[i] += (int64_t)tab[20 * k + 1 + 3 * i + j] * q[j];
-        qg[i] += (int64_t)tab[20 * k + 10 + 3 * i + j] * q[j];
-      }
-  }
-  const int n_in = type < 4 ? 4 : 2;  // elements inside: face 4, edge 2
   const int64_t nidx = (int64_t)z * d.plane + (int64_t)gj * d.nxp + gi;
-  int64_t dS[3];
-  for (int c = 0; c < 3; ++c) {
-    const int64_t qn = qprime(Un[c * d.comp + nidx]);
-    dS[c] = -(mul2_hi63(pg[c], qg[c], A1, A0, B1, B0) + mul_hi63(qn * (1024 - 128 * n_in), B1, B0));
+  int64_t qn[3];
+  for (int c = 0; c < 3; ++c) qn[c] = qprime(Un[c * d.comp + nidx]);
+  const TcMaterial mr = d.mats[(f.w >> 16) & 255];
+  const int Ar1 = (int)(mr.A >> 31), Ar0 = (int)(mr.A & 0x7FFFFFFF);
+  const int Br1 = (int)(mr.B >> 31), Br0 = (int)(mr.B & 0x7FFFFFFF);
+  int64_t dS[3] = {0, 0, 0};
+  for (int e = e0;;) {
+    const int mask = f.w & 255;
+    const int r0 = mask_idx[2 * mask], r1 = r0 + mask_idx[2 * mask + 1];
+    int64_t pg[3] = {0, 0, 0}, qg[3] = {0, 0, 0};
+    for (int r = r0; r < r1; ++r) {
+      const int16_t *row = mask_rows + 20 * r;
+      const int off = row[0];
+      const int ni = gi + off % 3 - 1, nj = gj + (off / 3) % 3 - 1, nk = z + off / 9 - 1;
+      if (ni < 0 || nj < 0 || nk < 0 || ni > d.nx || nj > d.ny || nk > d.nz) continue;
+      const int64_t nb = (int64_t)nk * d.plane + (int64_t)nj * d.nxp + ni;
+      int64_t q[3];
+      for (int j = 0; j < 3; ++j) q[j] = qprime(Un[j * d.comp + nb]);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          pg[i] += (int64_t)row[1 + 3 * i + j] * q[j];
+          qg[i] += (int64_t)row[10 + 3 * i + j] * q[j];
+        }
+    }
+    const TcMaterial mf = d.mats[(f.w >> 8) & 255];
+    const int Af1 = (int)(mf.A >> 31), Af0 = (int)(mf.A & 0x7FFFFFFF);
+    const int Bf1 = (int)(mf.B >> 31), Bf0 = (int)(mf.B & 0x7FFFFFFF);
+    const int64_t w = 128 * __popc(mask);
+    for (int c = 0; c < 3; ++c)
+      dS[c] += mul2_hi63(pg[c], qg[c], Af1, Af0, Bf1, Bf0) + mul_hi63(qn[c] * w, Bf1, Bf0) -
+               mul2_hi63(pg[c], qg[c], Ar1, Ar0, Br1, Br0) - mul_hi63(qn[c] * w, Br1, Br0);
+    if (++e >= d.n_fix) break;
+    f = d.fix[e];
+    if (!(f.w & ST_FIX_CONT)) break;
   }
   if (MODE == TC_MODE_KU) {
     for (int c = 0; c < 3; ++c) d.S_out[c * d.comp + nidx] += dS[c];
-    return;
+    return 0;
   }
   const int64_t cn = d.C[nidx];
-  if (cn == 0) return;  // fixed or massless: left at zero
+  if (cn == 0) return 0;  // fixed or massless: left at zero
   const int Rseg = P.eCref + P.rs - shq - 63;
   const int C1 = (int)(cn >> 31), C0 = (int)(cn & 0x7FFFFFFF);
   unsigned long long orv = 0;
@@ -206,50 +250,45 @@ __device__ void face_fix_node(const TcDevice &d, const TcStepParams &P, const in
     d.U_next[c * d.comp + nidx] = un;
     orv |= (unsigned long long)(un ^ (un >> 63));
   }
-  if (orv) {
-    unsigned long long *cur = d.or_slots + (size_t)P.or_slot * (1 + d.tiles_x * d.tiles_y);
-    atomicOr(&cur[1 + (gj / TC_OWN) * d.tiles_x + gi / TC_OWN], orv);
-    atomicOr(&cur[0], orv);
-  }
+  col = (gj / TC_OWN) * d.tiles_x + gi / TC_OWN;
+  return orv;
 }
 
-// one thread per listed face node (i, j, k, type | material << 8), after the
-// stencil kernel on the same stream
 template <int MODE>
-__global__ void __launch_bounds__(256) stencil_face_fix_kernel(const TcDevice d) {
+__global__ void __launch_bounds__(256) stencil_fix_kernel(const TcDevice d) {
   const TcStepParams P = *d.params;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < d.n_face;
-       idx += gridDim.x * blockDim.x) {
-    const int4 f = d.face[idx];
-    const int gi = f.x, gj = f.y, z = f.z, type = f.w & 255, mat = f.w >> 8;
-    // the digit shift of the node's column, as the stencil kernel takes it
-    int shq = P.shq;
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trips, so that the time step's bounds are OR-reduced per
+  // warp before the atomics (one per warp for the global word, one per
+  // group of lanes of one column for the column words)
+  for (int w0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < d.n_fix;
+       w0 += gridDim.x * blockDim.x) {
+    const int e0 = w0 + lane;
+    const int4 f = e0 < d.n_fix ? d.fix[e0] : make_int4(0, 0, 0, ST_FIX_CONT);
+    int col = -1;
+    // a continuation entry is handled with its node's first entry
+    const unsigned long long orv = (f.w & ST_FIX_CONT) ? 0ull : fix_node<MODE>(d, P, e0, f, col);
     if (MODE == TC_MODE_STEP) {
-      const int tx = gi / TC_OWN, ty = gj / TC_OWN;
-      const unsigned long long *prev =
-          d.or_slots + (size_t)((P.or_slot + 2) % 3) * (1 + d.tiles_x * d.tiles_y) + 1;
-      unsigned long long o = 0;
-      for (int dyc = -1; dyc <= 1; ++dyc)
-        for (int dxc = -1; dxc <= 1; ++dxc) {
-          const int cx = tx + dxc, cy = ty + dyc;
-          if (cx >= 0 && cy >= 0 && cx < d.tiles_x && cy < d.tiles_y) o |= prev[cy * d.tiles_x + cx];
-        }
-      const int b = o ? 64 - __clzll((long long)o) : 0;
-      shq = min(P.shq, max(0, b - TC_QBITS));
+      unsigned long long *cur = d.or_slots + (size_t)P.or_slot * (1 + d.tiles_x * d.tiles_y);
+      const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)orv);
+      const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(orv >> 32));
+      if (lane == 0 && (lo | hi)) atomicOr(&cur[0], ((unsigned long long)hi << 32) | lo);
+      const unsigned grp = __match_any_sync(0xffffffffu, col);
+      const unsigned glo = __reduce_or_sync(grp, (unsigned)orv);
+      const unsigned ghi = __reduce_or_sync(grp, (unsigned)(orv >> 32));
+      if (col >= 0 && lane == __ffs(grp) - 1 && (glo | ghi))
+        atomicOr(&cur[1 + col], ((unsigned long long)ghi << 32) | glo);
     }
-    const TcMaterial mt = d.mats[mat];
-    face_fix_node<MODE>(d, P, d.U_cur, gi, gj, z, type, (int)(mt.A >> 31), (int)(mt.A & 0x7FFFFFFF),
-                        (int)(mt.B >> 31), (int)(mt.B & 0x7FFFFFFF), shq);
   }
 }
 
-cudaError_t stencil_face_fix(cudaStream_t s, const TcDevice &d, int mode) {
-  if (d.n_face <= 0 || d.n_ctas <= 0) return cudaSuccess;
-  const int blocks = (d.n_face + 255) / 256 < 1024 ? (d.n_face + 255) / 256 : 1024;
+cudaError_t stencil_fix(cudaStream_t s, const TcDevice &d, int mode) {
+  if (d.n_fix <= 0 || d.n_ctas <= 0) return cudaSuccess;
+  const int blocks = (d.n_fix + 255) / 256 < 1024 ? (d.n_fix + 255) / 256 : 1024;
   if (mode == TC_MODE_STEP)
-    stencil_face_fix_kernel<TC_MODE_STEP><<<blocks, 256, 0, s>>>(d);
+    stencil_fix_kernel<TC_MODE_STEP><<<blocks, 256, 0, s>>>(d);
   else if (mode == TC_MODE_KU)
-    stencil_face_fix_kernel<TC_MODE_KU><<<blocks, 256, 0, s>>>(d);
+    stencil_fix_kernel<TC_MODE_KU><<<blocks, 256, 0, s>>>(d);
   else
     return cudaSuccess;
   return cudaGetLastError();
@@ -272,6 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int4 *seginfo = reinterpret_cast<int4 *>(smem + kOffSeg);  // 3 int4 per segment
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..7 U slots, 8,9 TMEM bufs
   uint32_t *misc = reinterpret_cast<uint32_t *>(smem + kOffMisc);  // [0] tmem base, [1] abort, [2] copies issued
+  int4 *limbs = reinterpret_cast<int4 *>(smem + kOffLimb);
 
   const int tid = threadIdx.x;
   const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0), lane = tid & 31;
@@ -303,6 +343,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   for (int i = tid; i < kBBytes / 16; i += kThreads)
     reinterpret_cast<uint4 *>(bimg)[i] = reinterpret_cast<const uint4 *>(d.Bst)[i];
+  for (int i = tid; i <= TC_MAX_MAT; i += kThreads) {
+    const TcMaterial mt = d.mats[i];
+    limbs[i] = make_int4((int)(mt.A >> 31), (int)(mt.A & 0x7FFFFFFF), (int)(mt.B >> 31),
+                         (int)(mt.B & 0x7FFFFFFF));
+  }
   {  // the unused K rows 12..15 of every node row block: the constant 256,
      // which the stencil images meet with zeros and the bias image with
      // 12288 (the digitisers never write these rows)
@@ -583,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   };
   // ---- output cursor and the epilogue's view of its segment ---------------
   int o = 0, osg = sbeg, oz = 0, oz1 = 0, gin = 1;  // output o: plane oz, input gin
-  int A1 = 0, A0 = 0, B1 = 0, B0 = 0, gi = 0, gj = 0, e_xo = 0, e_shq = 0, Rseg = 0;
+  int gi = 0, gj = 0, e_xo = 0, e_shq = 0, Rseg = 0;
   bool own = false;
   auto out_seek = [&](int sg) {
     osg = sg;
@@ -594,10 +639,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     oz = s.z;
     oz1 = s.w;
     if (!epi) return;
-    A1 = mat.x;
-    A0 = mat.y;
-    B1 = mat.z;
-    B0 = mat.w;
     const int X0 = TC_OWN * s.x - 1, Y0 = TC_OWN * s.y - 1;
     e_xo = X0 & 1;  // offset of the copied box, whose x start is even
     gi = X0 + xl;
@@ -606,17 +647,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     e_shq = shq;
     Rseg = P.eCref + P.rs - e_shq - 63;
   };
-  // the update's global operands (u^{n-1} and the multiplier C of the node)
-  // are loaded one output ahead
+  // the node's reference material and the update's global operands
+  // (u^{n-1} and the multiplier C of the node) are loaded one output ahead
   int64_t nx_uprev[3] = {0, 0, 0}, nx_cn = 0;
+  int nx_mat = ST_NO_MAT;
   auto load_update_at = [&](int4 s, int z) {
-    if (MODE == TC_MODE_STEP && epi) {
+    if (MODE != TC_MODE_PARTIALS && epi) {
       const int i = TC_OWN * s.x - 1 + xl, j = TC_OWN * s.y - 1 + yl;
       if (xl <= TC_OWN && yl <= TC_OWN && i <= d.nx && j <= d.ny) {
         const int64_t n = (int64_t)z * d.plane + (int64_t)j * d.nxp + i;
-        nx_cn = d.C[n];
+        nx_mat = d.node_mat[n];
+        if (MODE == TC_MODE_STEP) {
+          nx_cn = d.C[n];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) nx_uprev[c] = d.U_prev[c * d.comp + n];
+          for (int c = 0; c < 3; ++c) nx_uprev[c] = d.U_prev[c * d.comp + n];
+        }
       }
     }
   };
@@ -645,7 +690,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t nidx = (int64_t)oz * d.plane + (int64_t)gj * d.nxp + gi;
     const int64_t uprev[3] = {nx_uprev[0], nx_uprev[1], nx_uprev[2]};
     const int64_t cn = nx_cn;
-    if (MODE == TC_MODE_STEP && epi) {
+    const int mcur = nx_mat;  // the node's reference material
+    if (MODE != TC_MODE_PARTIALS && epi) {
       if (oz + 1 < oz1) {
         load_update_at(seg_at(osg), oz + 1);
       } else if (osg + 1 < send) {
@@ -723,6 +769,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       } else {
+        const int4 lm = limbs[mcur];
+        const int A1 = lm.x, A0 = lm.y, B1 = lm.z, B0 = lm.w;
         int64_t S[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)

@@ -10,10 +10,13 @@ part.  Checked here
   closed form of the element (independent of the library), zero outside the
   mesh;
 * K u against the FP64 oracle, on meshes with uniform blocks, material
-  interfaces and voids (these two go to the element kernel) and mesh faces
-  (on meshes of 8 Mi elements or more, a correction after the stencil
-  kernel subtracts the elements outside the mesh at the face nodes), and
-  against the element kernel alone (stencil off);
+  interfaces, voids and mesh faces, and against the element kernel alone
+  (stencil off).  Without per-node corrections only the uniform runs go to
+  the stencil kernel; with them (meshes of 8 Mi elements or more, or
+  stencil=2) every column-plane does, each node taking the most frequent
+  material around it, and a correction launch after the kernel exchanges
+  the material of the node's other elements (another material, void, or
+  outside the mesh);
 * time steps from a state and from rest (source, receivers) against the
   oracle, and the state after steps with the stencil on and off.
 """
@@ -90,17 +93,20 @@ def test_stencil_partials_bit_exact(shape, faces):
     nx, ny, nz = shape
     idx = np.flatnonzero(cov)
     i, j, k = idx % (nx + 1), (idx // (nx + 1)) % (ny + 1), idx // ((nx + 1) * (ny + 1))
-    on_face = (i == 0) | (i == nx) | (j == 0) | (j == ny)
-    if faces:   # face and edge nodes of the mesh are covered too
+    on_face = (i == 0) | (i == nx) | (j == 0) | (j == ny) | (k == 0) | (k == nz)
+    if faces:   # face, edge and corner nodes, and the material interfaces
         assert ((i == 0) | (i == nx)).any() and ((j == 0) | (j == ny)).any()
         assert (((i == 0) | (i == nx)) & ((j == 0) | (j == ny))).any()
+        assert (k == 0).any() and (k == nz).any() and (k == nz // 2).any()
+        assert ((k == 0) & (i == 0) & (j == 0)).any()
     else:
         assert not on_face.any()
     P = np.zeros((len(idx), 3), dtype=np.int64)
     Q = np.zeros((len(idx), 3), dtype=np.int64)
     for (ox, oy, oz), blk in Sk.items():
-        # a neighbour outside the mesh (x or y faces) holds zero
-        inside = (i + ox >= 0) & (i + ox <= nx) & (j + oy >= 0) & (j + oy <= ny)
+        # a neighbour outside the mesh holds zero
+        inside = ((i + ox >= 0) & (i + ox <= nx) & (j + oy >= 0) & (j + oy <= ny) &
+                  (k + oz >= 0) & (k + oz <= nz))
         nb = np.where(inside, (i + ox) + (nx + 1) * ((j + oy) + (ny + 1) * (k + oz)), 0)
         qn = q[nb] * inside[:, None]
         P += qn @ blk.T
@@ -119,7 +125,7 @@ def test_stencil_ku_matches_oracle(orc, shape, void_top):
     u = W.random_displacement(mesh, 7)
     ref = orc.ku(0, mesh, u)
     res = {}
-    for on in (2, True, False):   # with the face nodes, without, element kernel only
+    for on in (2, True, False):   # per-node corrections, uniform runs only, element kernel only
         with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False, stencil=on) as m:
             res[on] = m.internal_force(u)
         assert rel_max(res[on], ref) <= KU_TOL, on
@@ -150,9 +156,10 @@ def test_stencil_steps_from_state(orc, nsteps):
         assert rel_max(ugm, umo) <= 1e-13, on
 
 
-def test_stencil_face_nodes_steps_from_state(orc):
-    """The stencil kernel on the runs at the mesh faces (stencil=2), its face
-    nodes corrected after it: steps from a state against the oracle."""
+def test_stencil_corrected_nodes_steps_from_state(orc):
+    """Every column-plane in the stencil kernel (stencil=2), the nodes at the
+    material and void interfaces and the mesh faces corrected after it:
+    steps from a state against the oracle."""
     mesh = layered((47, 40, 12), void_top=2)
     mass = orc.node_mass(0, mesh)
     nx, ny, _ = mesh["shape"]
@@ -164,7 +171,8 @@ def test_stencil_face_nodes_steps_from_state(orc):
     dt = orc.dt(0, mesh, 0.5)
     _, uo, umo = orc.run(0, mesh, dt, 5, u0=u, um1=um, return_state=True)
     with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False, stencil=2) as m:
-        assert vfe.vfe_get_launches_per_step(m.handle) == 4
+        # prologue, stencil kernel, corrections (no plane left to the element kernel)
+        assert vfe.vfe_get_launches_per_step(m.handle) == 3
         vfe.vfe_set_state(m.handle, u, um)
         m.step(5)
         ug, ugm = vfe.vfe_get_state(m.handle)
@@ -219,3 +227,80 @@ def test_stencil_multi_plane_steps_on_off(orc, nsteps):
     err_on, err_off = rel_max(got[True], uo), rel_max(got[False], uo)
     assert err_off <= 1e-13
     assert err_on <= 1e-13, (err_on, np.argmax(np.abs(got[True] - uo)) // 3)
+
+
+# per-node corrections where several materials and voids meet at one node
+# (several correction entries per node) and on the dipping-layer generator
+def _blocky(shape, seed):
+    """Four materials and voids in 3x3x3 blocks: nodes where up to eight
+    values meet, voids touching the mesh faces."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    blocks = rng.integers(-1, 4, size=((nz + 2) // 3, (ny + 2) // 3, (nx + 2) // 3))
+    mat = blocks.repeat(3, 0).repeat(3, 1).repeat(3, 2)[:nz, :ny, :nx]
+    table = [[1800.0, 700.0, 2000.0], [2600.0, 1100.0, 2200.0], [1500.0, 500.0, 1900.0],
+             [3100.0, 1500.0, 2500.0]]
+    return W._mesh(shape, 1.0, mat, table, W._source((nx // 2, ny // 2, nz // 2), 60.0), [], 40,
+                   "blocky_%dx%dx%d" % shape)
+
+
+CORR_MESHES = [("blocky", lambda: _blocky((37, 34, 14), 5)),
+               ("random", lambda: W.random_mesh(6, shape=(33, 31, 9), n_mat=4, void_frac=0.2,
+                                                h=1.0)),
+               ("dipping", lambda: W.config3(shape=(48, 44, 24)))]
+
+
+@pytest.mark.parametrize("name,make", CORR_MESHES)
+def test_stencil_corrections_ku_matches_oracle(orc, name, make):
+    mesh = make()
+    u = W.random_displacement(mesh, 27)
+    ref = orc.ku(0, mesh, u)
+    with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False, stencil=2) as m:
+        out, cov, _, _ = vfe.vfe_debug_stencil_partials(m.handle, u)
+        f = m.internal_force(u)
+    # nearly every node with a solid element is in a stencil run
+    solid = orc.node_mass(0, mesh) > 0
+    assert cov[solid].mean() > 0.9
+    assert rel_max(f, ref) <= KU_TOL
+    assert not f.reshape(-1, 3)[~solid].any()
+
+
+@pytest.mark.parametrize("name,make", CORR_MESHES)
+def test_stencil_corrections_steps_match_oracle(orc, name, make):
+    mesh = make()
+    mass = orc.node_mass(0, mesh)
+    nx, ny, _ = mesh["shape"]
+    free = mass > 0
+    free[: (nx + 1) * (ny + 1)] = False
+    rng = np.random.default_rng(28)
+    u = rng.uniform(-1e-3, 1e-3, 3 * len(mass)) * np.repeat(free, 3)
+    um = u + rng.uniform(-1e-5, 1e-5, len(u)) * np.repeat(free, 3)
+    dt = orc.dt(0, mesh, 0.5)
+    _, uo, umo = orc.run(0, mesh, dt, 4, u0=u, um1=um, return_state=True)
+    for on in (2, False):
+        with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False, stencil=on) as m:
+            vfe.vfe_set_state(m.handle, u, um)
+            m.step(4)
+            ug, ugm = vfe.vfe_get_state(m.handle)
+        assert rel_max(ug, uo) <= 1e-13, on
+        assert rel_max(ugm, umo) <= 1e-13, on
+
+
+def test_stencil_corrections_traces_from_rest(orc):
+    """Dipping layers under a void top with the source and the receivers
+    (their planes in the element kernel, the rest in the stencil kernel with
+    corrections): 150 steps against the oracle's traces."""
+    mesh = W.config3(shape=(48, 44, 24))
+    si, sj, sk = mesh["source"]["ijk"]
+    # receivers a few nodes from the source, so that the wave reaches them
+    mesh["receivers"] = np.array([(si + a, sj + b, sk + c) for a, b, c in
+                                  ((4, 0, 0), (-3, 2, 0), (0, -4, 1), (2, 3, -3), (-4, -4, 2),
+                                   (5, 1, -2), (0, 0, 5), (-2, 5, -4))], dtype=np.int32)
+    dt = orc.dt(0, mesh, 0.5)
+    n = 150
+    ref = orc.run(0, mesh, dt, n, source=oracle_source(mesh), receivers=W.receiver_nodes(mesh))
+    with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, stencil=2) as m:
+        assert vfe.vfe_get_launches_per_step(m.handle) == 4
+        m.step(n)
+        tr = m.traces()
+    assert rel_l2(tr, ref) <= 1e-9
