@@ -220,7 +220,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
-# roofline bookkeeping for the dominant kernel (tc_step_kernel)
+# roofline bookkeeping for one time step (the dominant unit: all its kernels)
 # --------------------------------------------------------------------------
 def algorithmic_bytes_per_step(mesh, damped=False):
     """HBM bytes one time step must move at minimum: read u^n, u^{n-1} and the
@@ -460,10 +460,12 @@ def run_ours(args):
             "frac": achieved / float(peaks["hbm_gbs"]),
             "traffic": prof["dram_bytes"] if prof else None,
             "algorithmic_bytes_per_launch": abytes, "peak_source": peak_src,
-            "kernel": "one time step: tc_prologue_kernel, then tc_step_kernel (mixed and "
-                      "boundary column-planes) and tc_stencil_kernel (uniform column-planes) "
-                      "as programmatic dependents that overlap; duration = the step's CUDA-event "
-                      "time"}
+            "kernel": "one time step: tc_prologue_kernel, then tc_step_kernel (the source "
+                      "and receiver planes, and the non-uniform ones on meshes below 8 Mi "
+                      "elements) and tc_stencil_kernel (every other column-plane, per-node "
+                      "material) as programmatic dependents that overlap, then "
+                      "stencil_fix_kernel (nodes with elements of another material, void or "
+                      "outside the mesh); duration = the step's CUDA-event time"}
     # the tensor pipe's share: fp16-digit multiply-adds per second against the
     # measured dense bf16 rate (fp16 runs at the same rate)
     tc_tops = tc_ops_per_element(args.stages) * ne / (ms_step * 1e-3) / 1e12
