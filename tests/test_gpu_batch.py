@@ -100,3 +100,29 @@ def test_batch_fewer_stages_equals_individual_runs():
             assert np.array_equal(m.traces(), tr)
     for m in meshes:
         m.close()
+
+
+def test_batch_with_node_corrections_equals_individual_runs():
+    """Meshes with per-node corrections (stencil=2: every column-plane but
+    the source and receiver planes in the stencil kernel, the interface,
+    void and face nodes corrected after it, on the batch's side streams)
+    beside meshes without: bit-identical to each mesh alone."""
+    models = [W.config3(shape=(48, 44, 24)), W.random_mesh(75, shape=(21, 18, 11), void_frac=0.15),
+              _models()[2], _models()[5]]
+    opts = [2, 2, 1, 2]
+    nsteps = 11
+    alone = []
+    for w, st in zip(models, opts):
+        with vfe.Mesh(w, stencil=st) as m:
+            m.step(nsteps)
+            alone.append((vfe.vfe_get_state(m.handle), m.traces()))
+    meshes = [vfe.Mesh(w, stencil=st) for w, st in zip(models, opts)]
+    with vfe.Batch(meshes) as b:
+        b.step(nsteps)
+        b.synchronize()
+        for m, (state, tr) in zip(meshes, alone):
+            u, um = vfe.vfe_get_state(m.handle)
+            assert np.array_equal(u, state[0]) and np.array_equal(um, state[1])
+            assert np.array_equal(m.traces(), tr)
+    for m in meshes:
+        m.close()

@@ -36,10 +36,12 @@ def _noalloc_via_cabi(handle, u):
     return f
 
 
+@pytest.mark.parametrize("stencil", [1, 2])   # 2: per-node corrections in the stencil kernel
 @pytest.mark.parametrize("shape", [(17, 16, 6), (33, 31, 9)])
-def test_noalloc_matches_oracle_and_internal_force_twice(orc, shape):
+def test_noalloc_matches_oracle_and_internal_force_twice(orc, shape, stencil):
     mesh = W.random_mesh(300 + sum(shape), shape=shape, void_frac=0.1)
-    with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False) as m:
+    with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False,
+                  stencil=stencil) as m:
         for seed, scale in ((1, 1e-3), (2, 7e-9)):
             u = W.random_displacement(mesh, seed, scale=scale)
             want = orc.ku(0, mesh, u)
