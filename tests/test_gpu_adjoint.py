@@ -37,6 +37,21 @@ def test_gradient_matches_oracle_adjoint(orc, path, tol, checkpoint):
     assert np.abs(g - g_ref).max() <= tol * np.abs(g_ref).max()
 
 
+def test_gradient_with_node_corrections_matches_oracle_adjoint(orc):
+    """The TC gradient with every column-plane but the source and receiver
+    planes in the stencil kernel (stencil=2: per-node material, the layer
+    interface and face nodes corrected), forward and adjoint runs."""
+    obs, bg = small_problem(n=16, nsteps=60)
+    n = bg["nsteps"]
+    dt = orc.dt(0, obs, 0.5)
+    data, src = _oracle_data(orc, obs, dt, n)
+    g_ref, J_ref = orc.misfit_gradient(0, bg, dt, n, src, W.receiver_nodes(bg), data)
+    with vfe.Mesh(bg, path=vfe.VFE_PATH_TC, dt=dt, stencil=2) as m:
+        g, J = vfe.vfe_misfit_gradient(m.handle, data, 20)
+    assert J == pytest.approx(J_ref, rel=1e-6)
+    assert np.abs(g - g_ref).max() <= 1e-6 * np.abs(g_ref).max()
+
+
 def test_gradient_matches_finite_differences():
     obs, bg = small_problem(n=12, nsteps=60)
     with vfe.Mesh(obs, path=vfe.VFE_PATH_FP64) as m:
