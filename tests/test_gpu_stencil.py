@@ -304,3 +304,36 @@ def test_stencil_corrections_traces_from_rest(orc):
         m.step(n)
         tr = m.traces()
     assert rel_l2(tr, ref) <= 1e-9
+
+
+EDGE_SHAPES = [(1, 1, 1), (2, 3, 1), (5, 4, 2), (14, 16, 3), (16, 14, 2), (31, 1, 5), (15, 15, 4)]
+
+
+@pytest.mark.parametrize("shape", EDGE_SHAPES)
+def test_stencil_corrections_edge_meshes(orc, shape):
+    """Per-node corrections (stencil=2) on meshes one or two elements thick,
+    narrower than a node column (both x faces in one column), single
+    elements, and with voids: K u and three steps from a state against the
+    oracle."""
+    mesh = W.random_mesh(400 + sum(shape), shape=shape, n_mat=3, void_frac=0.25, h=1.0)
+    if not (mesh["material_ids"] >= 0).any():
+        mesh["material_ids"][0] = 0
+    u = W.random_displacement(mesh, 5)
+    ref = orc.ku(0, mesh, u)
+    mass = orc.node_mass(0, mesh)
+    nx, ny, _ = mesh["shape"]
+    free = mass > 0
+    free[: (nx + 1) * (ny + 1)] = False
+    rng = np.random.default_rng(6)
+    us = rng.uniform(-1e-3, 1e-3, 3 * len(mass)) * np.repeat(free, 3)
+    um = us + rng.uniform(-1e-5, 1e-5, len(us)) * np.repeat(free, 3)
+    dt = orc.dt(0, mesh, 0.5)
+    _, uo, umo = orc.run(0, mesh, dt, 3, u0=us, um1=um, return_state=True)
+    with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, source=False, receivers=False, stencil=2) as m:
+        f = m.internal_force(u)
+        vfe.vfe_set_state(m.handle, us, um)
+        m.step(3)
+        ug, ugm = vfe.vfe_get_state(m.handle)
+    assert rel_max(f, ref) <= KU_TOL
+    assert rel_max(ug, uo) <= 1e-13
+    assert rel_max(ugm, umo) <= 1e-13
