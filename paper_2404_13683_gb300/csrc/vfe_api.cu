@@ -190,15 +190,14 @@ struct vfe_mesh {
   int4 *d_all_segs = nullptr;
   int32_t *d_all_off = nullptr;
   int all_ctas = 0;
-  // node-stencil kernel on the uniform runs (stencil_on): its segments, their
-  // material, its CTA ranges, its B image and its tensor maps (box 20x18x1x3)
+  // node-stencil kernel on the stencil runs (stencil_on): its segments, its
+  // CTA ranges, its B image and its tensor maps (box 20x18x1x3)
   bool stencil_on = false;
   // the runs before their split over the CTAs (a batch splits them again):
-  // element-kernel runs, stencil runs and their materials
+  // element-kernel runs and stencil runs
   std::vector<int4> el_runs, st_runs;
-  std::vector<int32_t> st_rmat;
   std::vector<int4> st_segs;
-  std::vector<int32_t> st_mat, st_off;
+  std::vector<int32_t> st_off;
   int st_ctas = 0;
   // per-node material and corrections (meshes of ST_FIX_MIN_ELEMENTS or
   // more, or stencil option 2): every column-plane but the source and
@@ -209,7 +208,7 @@ struct vfe_mesh {
   int4 *d_fix = nullptr;
   int n_fix = 0;
   int4 *d_st_segs = nullptr;
-  int32_t *d_st_mat = nullptr, *d_st_off = nullptr;
+  int32_t *d_st_off = nullptr;
   uint16_t *d_Bst = nullptr;
   CUtensorMap st_tmap[2];
   int e_ref = 0, eC = 0;
@@ -283,12 +282,11 @@ static TcDevice tc_device(const vfe_mesh *m, int cur) {
   return d;
 }
 
-// the same arguments for the node-stencil kernel over the uniform runs
+// the same arguments for the node-stencil kernel over the stencil runs
 static TcDevice tc_stencil_device(const vfe_mesh *m, int cur) {
   TcDevice d = tc_device(m, cur);
   d.segs = m->d_st_segs;
   d.seg_off = m->d_st_off;
-  d.seg_mat = m->d_st_mat;
   d.n_ctas = m->stencil_on ? m->st_ctas : 0;
   d.Bst = m->d_Bst;
   d.U_cur = m->d_U[cur];  // u^n: the corrections read it
@@ -435,7 +433,7 @@ int vfe_destroy(vfe_mesh *m) {
                   m->d_recv_off, m->d_or, m->d_tcparams, m->d_tcpersist, m->d_segs,
                   m->d_seg_off, m->d_inj, m->d_force, m->d_w[0], m->d_w[1],
                   m->d_W[0], m->d_W[1], m->d_all_segs, m->d_all_off, m->d_st_segs,
-                  m->d_st_mat, m->d_st_off, m->d_Bst, m->d_elemB, m->d_elemG, m->d_kappa,
+                  m->d_st_off, m->d_Bst, m->d_elemB, m->d_elemG, m->d_kappa,
                   m->d_Kkg, m->d_fix, m->d_node_mat};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -730,7 +728,6 @@ static int build_segments(vfe_mesh *m) {
   m->fix_on = m->stencil_on &&
                (m->opt.stencil == 2 || (int64_t)nx * ny * nz >= ST_FIX_MIN_ELEMENTS);
   std::vector<int4> all_runs, el_runs, st_runs;
-  std::vector<int32_t> st_rmat;
   // the stencil runs' nodes: reference material, correction entries
   std::vector<uint8_t> node_mat(m->stencil_on ? (size_t)m->comp : 0, (uint8_t)ST_NO_MAT);
   std::vector<int4> fix;
@@ -769,13 +766,12 @@ static int build_segments(vfe_mesh *m) {
         layer[ez] = v;
       }
       int run_cls = -3, run_z0 = 0;
-      // a uniform run of one plane goes to the element kernel (the stencil
+      // a stencil run of one plane goes to the element kernel (the stencil
       // kernel's segments own two planes or more); element runs that touch
       // are merged
       auto flush = [&](int z1) {
         if (run_cls >= 0 && z1 - run_z0 >= 2) {
           st_runs.push_back(make_int4(tx, ty, run_z0, z1));
-          st_rmat.push_back(run_cls);
         } else if (run_cls != -1 && run_cls != -3) {
           if (!el_runs.empty() && el_runs.back().x == tx && el_runs.back().y == ty &&
               el_runs.back().w == run_z0)
@@ -861,10 +857,9 @@ static int build_segments(vfe_mesh *m) {
   if ((rc = upload_vec(&m->d_all_off, all_off)) != VFE_OK) return rc;
   if (m->stencil_on) {
     split_runs(el_runs, nullptr, ctas, 2.0, m->segs, nullptr, m->seg_off);
-    split_runs(st_runs, &st_rmat, ctas, 0.0, m->st_segs, &m->st_mat, m->st_off, 2);
+    split_runs(st_runs, nullptr, ctas, 0.0, m->st_segs, nullptr, m->st_off, 2);
     m->el_runs = el_runs;
     m->st_runs = st_runs;
-    m->st_rmat = st_rmat;
     if (fix.size() > (size_t)INT32_MAX) return fail(VFE_EINVAL, "too many correction entries");
     for (const int4 &e : fix)
       if (e.x < 0 || e.x > nx || e.y < 0 || e.y > ny || e.z < 0 || e.z > nz ||
@@ -878,9 +873,7 @@ static int build_segments(vfe_mesh *m) {
     m->seg_off = all_off;
     m->el_runs.clear();
     m->st_runs.clear();
-    m->st_rmat.clear();
     m->st_segs.clear();
-    m->st_mat.clear();
     m->st_off.assign(1, 0);
     m->n_fix = 0;
   }
@@ -900,12 +893,9 @@ static int build_segments(vfe_mesh *m) {
   };
   if (bad_segs(m->segs, m->seg_off, 1) || (m->stencil_on && bad_segs(m->st_segs, m->st_off, 2)))
     return fail(VFE_EINVAL, "internal: inconsistent segment tables");
-  if (m->stencil_on && m->st_mat.size() != m->st_segs.size())
-    return fail(VFE_EINVAL, "internal: inconsistent segment tables");
   if ((rc = upload_vec(&m->d_segs, m->segs)) != VFE_OK) return rc;
   if ((rc = upload_vec(&m->d_seg_off, m->seg_off)) != VFE_OK) return rc;
   if ((rc = upload_vec(&m->d_st_segs, m->st_segs)) != VFE_OK) return rc;
-  if ((rc = upload_vec(&m->d_st_mat, m->st_mat)) != VFE_OK) return rc;
   if ((rc = upload_vec(&m->d_st_off, m->st_off)) != VFE_OK) return rc;
   invalidate_graphs(m);
   return VFE_OK;
@@ -1687,7 +1677,7 @@ static int tc_apply(vfe_mesh *m, const double *u, int mode, std::vector<int64_t>
       rc = fail(VFE_ECUDA, "K u kernel: %s", cudaGetErrorString(e));
       break;
     }
-    if (mode == TC_MODE_KU && m->stencil_on) {  // the uniform runs
+    if (mode == TC_MODE_KU && m->stencil_on) {  // the stencil runs
       TcDevice ds = tc_stencil_device(m, m->cur);
       ds.params = dp;
       ds.S_out = dout;
@@ -2103,14 +2093,14 @@ struct vfe_batch {
   TcDevice *d_devs[2] = {nullptr, nullptr};
   CUtensorMap *d_maps[2] = {nullptr, nullptr};
   TcPrologueArgs *d_pro = nullptr;
-  // meshes with the node-stencil kernel: their uniform runs go to one stencil
+  // meshes with the node-stencil kernel: their stencil runs go to one stencil
   // launch per mesh, split over a share of the SMs in proportion to the
   // mesh's planes, on side streams that run side by side with the batched
   // element kernel (the two touch disjoint nodes of each mesh)
   struct StencilPart {
     int mesh, n_ctas;
     int4 *d_segs;
-    int32_t *d_off, *d_mat;
+    int32_t *d_off;
   };
   std::vector<StencilPart> st_parts;
   std::vector<cudaStream_t> side;
@@ -2128,7 +2118,6 @@ static void batch_free_arrays(vfe_batch *b) {
   for (vfe_batch::StencilPart &q : b->st_parts) {
     if (q.d_segs) cudaFree(q.d_segs);
     if (q.d_off) cudaFree(q.d_off);
-    if (q.d_mat) cudaFree(q.d_mat);
   }
   b->st_parts.clear();
   b->d_segs = nullptr; b->d_seg_mesh = nullptr; b->d_seg_off = nullptr; b->d_recv_off = nullptr;
@@ -2184,7 +2173,7 @@ static int batch_build(vfe_batch *b) {
     b->seg_mesh.insert(b->seg_mesh.end(), gmesh.begin(), gmesh.end());
     b->groups.push_back(grp);
   }
-  // the stencil parts: each mesh's uniform runs over its share of the SMs
+  // the stencil parts: each mesh's stencil runs over its share of the SMs
   {
     int64_t all = 0;
     for (int i = 0; i < nm; ++i)
@@ -2197,20 +2186,18 @@ static int batch_build(vfe_batch *b) {
       const int ctas = (int)std::max<int64_t>(
           1, std::min<int64_t>(b->sms, (planes * b->sms + all / 2) / all));
       std::vector<int4> psegs;
-      std::vector<int32_t> pmat, poff;
-      split_runs(m->st_runs, &m->st_rmat, ctas, 0.0, psegs, &pmat, poff, 2);
+      std::vector<int32_t> poff;
+      split_runs(m->st_runs, nullptr, ctas, 0.0, psegs, nullptr, poff, 2);
       vfe_batch::StencilPart q;
       q.mesh = i;
       q.n_ctas = (int)poff.size() - 1;
       q.d_segs = nullptr;
       q.d_off = nullptr;
-      q.d_mat = nullptr;
       b->st_parts.push_back(q);
       vfe_batch::StencilPart &qq = b->st_parts.back();
       int rc;
       if ((rc = upload_vec(&qq.d_segs, psegs)) != VFE_OK) return rc;
       if ((rc = upload_vec(&qq.d_off, poff)) != VFE_OK) return rc;
-      if ((rc = upload_vec(&qq.d_mat, pmat)) != VFE_OK) return rc;
     }
   }
   // receivers per batch segment (indices into each mesh's own trace rows)
@@ -2330,7 +2317,6 @@ static int batch_enqueue(vfe_batch *b, int parity) {
       TcDevice d = tc_stencil_device(m, cur);
       d.segs = q.d_segs;
       d.seg_off = q.d_off;
-      d.seg_mat = q.d_mat;
       d.n_ctas = q.n_ctas;
       CUDA_TRY(stencil_launch_ex(b->side[k % ns], d, &m->st_tmap[cur], TC_MODE_STEP, false));
       CUDA_TRY(stencil_fix(b->side[k % ns], d, TC_MODE_STEP));

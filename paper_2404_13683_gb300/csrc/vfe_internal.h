@@ -38,7 +38,7 @@
 // source and receiver planes to the stencil kernel, with per-node material
 // and a correction launch for the nodes whose eight elements are not all of
 // that material (material and void interfaces, the mesh faces); smaller
-// meshes give it the uniform runs alone (no correction launch)
+// meshes give it the uniform runs alone
 #define ST_FIX_MIN_ELEMENTS (8LL << 20)
 // per-node reference material of the stencil kernel: a material index, or
 // ST_NO_MAT (no solid element; the material table's zero entry)
@@ -129,7 +129,6 @@ struct TcDevice {         // everything the TC kernels read (by value)
   // buffer (B images, then the correction table), the reference material of
   // every node of its runs (mats[] has TC_MAX_MAT + 1 entries, zero beyond
   // n_mat); U_cur above holds u^n for the corrections
-  const int32_t *seg_mat;
   const uint16_t *Bst;
   const uint8_t *node_mat;
   // the correction entries of the stencil runs' nodes (stencil_fix, after
@@ -227,7 +226,7 @@ struct VfeMeshView {
   int tc;                 // 1 on the tensor-core path
   cudaStream_t stream;
   TcDevice dev;           // kernel arguments with the mesh's own pointers
-  int stencil_on;         // the node-stencil kernel takes the uniform runs
+  int stencil_on;         // the node-stencil kernel takes the stencil runs
   TcDevice st;            // its arguments (segments, materials, B image)
 };
 int vfe_mesh_view(vfe_mesh *mesh, VfeMeshView *view);
@@ -255,7 +254,7 @@ cudaError_t slab_unpack_tc(cudaStream_t s, int64_t *U, int nx, int ny, int nxp, 
                            int64_t comp, int k, const int64_t *persist, const double *in,
                            unsigned long long *slot, int tiles_x);
 cudaError_t stencil_prepare();
-// the node-stencil kernel over d.segs / d.seg_off / d.seg_mat (d.n_ctas CTAs;
+// the node-stencil kernel over d.segs / d.seg_off (d.n_ctas CTAs;
 // nothing is launched for 0); tmap: box ST_BOXX x ST_BOXY x 1 x 3
 cudaError_t stencil_launch(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode);
 cudaError_t stencil_launch_ex(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode,

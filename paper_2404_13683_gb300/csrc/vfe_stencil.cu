@@ -88,10 +88,10 @@ constexpr int kOffU = kOffD + kDSlots * kDSlotBytes;
 constexpr int kOffB = kOffU + kUSlots * kUStride;
 constexpr int kOffBias = kOffB + kBBytes;
 // the CTA's first kSegCap segments, staged once per launch: column and
-// planes, material multipliers and digit shift (48 bytes each); later
-// segments are read from global memory where they are needed
+// planes, and digit shift (32 bytes each); later segments are read from
+// global memory where they are needed
 constexpr int kSegCap = 256;
-constexpr int kSegInfoBytes = 48;
+constexpr int kSegInfoBytes = 32;
 constexpr int kOffSeg = kOffBias + kBiasBytes;
 constexpr int kOffBar = kOffSeg + kSegCap * kSegInfoBytes;
 constexpr int kOffMisc = kOffBar + 16 * 8;
@@ -298,7 +298,8 @@ cudaError_t stencil_fix(cudaStream_t s, const TcDevice &d, int mode) {
 // MODE: TC_MODE_STEP (time step), TC_MODE_KU (S of K u), TC_MODE_PARTIALS
 // (per node: P, the stencil part of Q and q', 9 int64 in component-stride
 // layout, for exact checks).  CTA b walks stencil segments seg_off[b] ..
-// seg_off[b+1]-1; segment (tx, ty, z0, z1) with material seg_mat[].
+// seg_off[b+1]-1; segment (tx, ty, z0, z1), each node with its material
+// node_mat[].
 // ---------------------------------------------------------------------------
 template <int MODE, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int64_t *uslot = reinterpret_cast<int64_t *>(smem + kOffU);
   unsigned char *bimg = smem + kOffB;
   unsigned char *bias_img = smem + kOffBias;
-  int4 *seginfo = reinterpret_cast<int4 *>(smem + kOffSeg);  // 3 int4 per segment
+  int4 *seginfo = reinterpret_cast<int4 *>(smem + kOffSeg);  // 2 int4 per segment
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffBar);  // 0..7 U slots, 8,9 TMEM bufs
   uint32_t *misc = reinterpret_cast<uint32_t *>(smem + kOffMisc);  // [0] tmem base, [1] abort, [2] copies issued
   int4 *limbs = reinterpret_cast<int4 *>(smem + kOffLimb);
@@ -416,31 +417,26 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     return shq;
   };
-  // segment table entry: {tx, ty, z0, z1}, {A1, A0, B1, B0}, {shq, -, -, -}
+  // segment table entry: {tx, ty, z0, z1}, {shq, -, -, -}
   auto seg_fill = [&](int sg, int4 *e) {
     const int4 s = d.segs[sg];
-    const TcMaterial mt = d.mats[d.seg_mat[sg]];
     e[0] = s;
-    e[1] = make_int4((int)(mt.A >> 31), (int)(mt.A & 0x7FFFFFFF), (int)(mt.B >> 31),
-                     (int)(mt.B & 0x7FFFFFFF));
-    e[2] = make_int4(seg_shq_global(s), 0, 0, 0);
+    e[1] = make_int4(seg_shq_global(s), 0, 0, 0);
   };
-  for (int i = tid; i < min(send - sbeg, kSegCap); i += kThreads) seg_fill(sbeg + i, seginfo + 3 * i);
+  for (int i = tid; i < min(send - sbeg, kSegCap); i += kThreads) seg_fill(sbeg + i, seginfo + 2 * i);
   __syncthreads();
   auto seg_at = [&](int sg) -> int4 {
-    return sg - sbeg < kSegCap ? seginfo[3 * (sg - sbeg)] : d.segs[sg];
+    return sg - sbeg < kSegCap ? seginfo[2 * (sg - sbeg)] : d.segs[sg];
   };
-  auto seg_entry = [&](int sg, int4 &s, int4 &mat, int &shq) {
+  auto seg_entry = [&](int sg, int4 &s, int &shq) {
     if (sg - sbeg < kSegCap) {
-      s = seginfo[3 * (sg - sbeg)];
-      mat = seginfo[3 * (sg - sbeg) + 1];
-      shq = seginfo[3 * (sg - sbeg) + 2].x;
+      s = seginfo[2 * (sg - sbeg)];
+      shq = seginfo[2 * (sg - sbeg) + 1].x;
     } else {
-      int4 e[3];
+      int4 e[2];
       seg_fill(sg, e);
       s = e[0];
-      mat = e[1];
-      shq = e[2].x;
+      shq = e[1].x;
     }
   };
 
@@ -487,8 +483,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   in_seek(mc, sbeg, 0);
   int d_shq = 0, d_xo = 0;  // digit cursor's column shift and box offset
   if (sbeg < send) {
-    int4 s, mat;
-    seg_entry(sbeg, s, mat, d_shq);
+    int4 s;
+    seg_entry(sbeg, s, d_shq);
     d_xo = (TC_OWN * s.x - 1) & 1;
   }
 
@@ -571,8 +567,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int sg = dc.sg;
       in_next(dc);
       if (dc.sg != sg && dc.sg < send) {
-        int4 s, mat;
-        seg_entry(dc.sg, s, mat, d_shq);
+        int4 s;
+        seg_entry(dc.sg, s, d_shq);
         d_xo = (TC_OWN * s.x - 1) & 1;
       }
     }
@@ -633,9 +629,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto out_seek = [&](int sg) {
     osg = sg;
     if (sg >= send) return;
-    int4 s, mat;
+    int4 s;
     int shq;
-    seg_entry(sg, s, mat, shq);
+    seg_entry(sg, s, shq);
     oz = s.z;
     oz1 = s.w;
     if (!epi) return;
@@ -902,7 +898,7 @@ static cudaError_t st_launch_mode(cudaStream_t s, const TcDevice &d, const CUten
   }
 }
 
-// d.segs / d.seg_off / d.seg_mat / d.n_ctas describe the stencil segments;
+// d.segs / d.seg_off / d.n_ctas describe the stencil segments;
 // pdl: a time step is launched as a programmatic dependent of the kernel
 // before it on the stream
 cudaError_t stencil_launch_ex(cudaStream_t s, const TcDevice &d, const CUtensorMap *tmap, int mode,
