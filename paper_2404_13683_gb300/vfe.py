@@ -427,7 +427,10 @@ class Batch:
 
 class Mesh:
     """Owning wrapper over a ``vfe_mesh*`` built from a workload dictionary
-    (see ``workloads.py``)."""
+    (see ``workloads.py``).  ``stencil``: the tensor-core path's node-stencil
+    option (``vfe_options.stencil``): True or 1 (default; per-node
+    corrections on meshes of 8 Mi elements or more), 2 (per-node
+    corrections on any mesh), False or 0 (the element kernel everywhere)."""
 
     def __init__(self, workload, path=VFE_PATH_TC, kind=VFE_OVFEM, stages=5, dt=None,
                  fix_bottom=None, stream=None, device=0, source=True, receivers=True,
