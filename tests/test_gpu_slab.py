@@ -29,10 +29,10 @@ def _model():
                    "slab_test_40x36x30")
 
 
-def _run_slabs(mesh, world, nsteps, path, dt):
+def _run_slabs(mesh, world, nsteps, path, dt, stencil=True):
     import torch
     slabs = [S.Slab(mesh, world, r, dt) for r in range(world)]
-    engines = [S.GpuSlabEngine(s, torch, path=path) for s in slabs]
+    engines = [S.GpuSlabEngine(s, torch, path=path, stencil=stencil) for s in slabs]
     # the slabs without the source size the fixed-point unit for it too
     scale = next(e.source_scale() for s, e in zip(slabs, engines) if s.workload["source"])
     for e in engines:
@@ -95,3 +95,23 @@ def test_slabs_match_whole_mesh(orc, world, path):
         assert rel_max(u_sl, u_one) <= 1e-12
         assert rel_l2(tr_sl, tr_one) <= 1e-9
         assert rel_l2(tr_sl, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slabs_with_node_corrections_match_whole_mesh(orc, world):
+    """Slabs and the whole mesh with per-node corrections (stencil=2: the
+    layer, inclusion and void interfaces and the faces, including each
+    slab's halo planes, corrected in the stencil kernel's runs)."""
+    mesh = _model()
+    nsteps = 40
+    dt = orc.dt(0, mesh, 0.5)
+    with vfe.Mesh(mesh, path=vfe.VFE_PATH_TC, dt=dt, stencil=2) as m:
+        m.step(nsteps)
+        u_one, _ = vfe.vfe_get_state(m.handle)
+        tr_one = m.traces()
+    u_sl, tr_sl = _run_slabs(mesh, world, nsteps, vfe.VFE_PATH_TC, dt, stencil=2)
+    ref = orc.run(0, mesh, dt, nsteps, source=oracle_source(mesh),
+                  receivers=W.receiver_nodes(mesh))
+    assert rel_max(u_sl, u_one) <= 1e-12
+    assert rel_l2(tr_sl, tr_one) <= 1e-9
+    assert rel_l2(tr_sl, ref) <= 1e-9
